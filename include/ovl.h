@@ -1,0 +1,169 @@
+/*
+ * ovl.h -- C ABI of the GB300 (sm_103a) library that approximates
+ *          y = sgn(H_w(mu)) b by deflated Arnoldi.
+ *
+ * Method: Bloch, Wettig, Frommer, Lang, "An iterative method to compute the
+ * overlap Dirac operator at nonzero chemical potential" (Lattice 2007,
+ * arXiv:0710.0341).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Lattice dims[4] = {Lx, Ly, Lz, Lt}; site index n = x + Lx*(y + Ly*(z + Lz*t)).
+ * Canonical spinor layout (host or device): complex128 psi[n][spin 4][colour 3]
+ *   stored as interleaved doubles (re, im): 24 doubles per site, N = 12 V complex.
+ * Canonical link layout: complex128 U[n][nu 0..3 = x,y,z,t][a 3][b 3], 72
+ *   doubles per direction and site, 288 per site.
+ * Gamma matrices: Hermitian chiral basis with gamma_5 = diag(1, 1, -1, -1)
+ *   (the paper says only "Euclidean"; this basis is the library's reading).
+ * Pointers: every double/float pointer may be host or device memory; the
+ *   library detects which (cudaPointerGetAttributes). Device pointers must
+ *   be on the lattice's device. The caller owns every buffer it passes; the
+ *   library owns its internal workspace (Krylov bases, deflation vectors,
+ *   Newton work) and frees it in the matching destroy call.
+ * Streams: work is issued on the stream given to ovl_create_lattice; every
+ *   call returns after the result is complete (it synchronises that stream),
+ *   so status codes are synchronous.
+ * Errors: every call returns 0 (OVL_OK) or one of the codes below and keeps a
+ *   message for ovl_last_error(). A failed call leaves its outputs undefined
+ *   and the handle usable.
+ * Threads: a handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef OVL_H
+#define OVL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OVL_OK        0
+#define OVL_EINVAL    1  /* bad argument: sizes, null pointers, mismatched mu/m_w */
+#define OVL_ENOMEM    2  /* device allocation failed or over the workspace budget */
+#define OVL_ECUDA     3  /* a CUDA runtime call failed */
+#define OVL_ENOCONV   4  /* Newton or eigensolver hit its iteration limit */
+#define OVL_ETIMEOUT  5  /* a device-side wait gave up after its iteration limit */
+#define OVL_ENOTSUP   6  /* combination not supported by this build */
+
+typedef struct ovl_lattice_s*    ovl_lattice;
+typedef struct ovl_deflation_s*  ovl_deflation;
+
+/* Arithmetic of the Arnoldi path (ovl_sign_params.prec). */
+#define OVL_PREC_FP64       0  /* FP64 stencil; basis stored as FP32 hi+lo pairs (48-bit);
+                                  FP64 Newton, projections and recombination */
+#define OVL_PREC_MIXED      1  /* FP32 stencil (18-real links), FP32 basis, FP64 coefficients */
+#define OVL_PREC_MIXED_R12  2  /* as OVL_PREC_MIXED with 12-real (two-row) links */
+
+/* Deflation scheme (Sec. 3 Schur, Sec. 4 LR). */
+#define OVL_DEFL_NONE   0
+#define OVL_DEFL_SCHUR  1
+#define OVL_DEFL_LR     2
+
+/* Packed (internal) spinor formats for the stencil-only entry points. */
+#define OVL_VEC_F64  0   /* complex128 */
+#define OVL_VEC_F32  1   /* complex64  */
+/* Link formats for the stencil-only entry points. */
+#define OVL_LINKS_F64  0
+#define OVL_LINKS_F32  1
+#define OVL_LINKS_R12  2
+
+typedef struct {
+    double mu;          /* chemical potential (Eq. 2) */
+    double m_w;         /* Wilson mass, kappa = 1/(8 + 2 m_w), m_w in (-2, 0) */
+    int    k;           /* Krylov depth (Eq. 7); 1 <= k */
+    int    prec;        /* OVL_PREC_* */
+    int    newton_max_iter;  /* <= 0: default 100 */
+    double newton_tol;       /* <= 0: default 1e-13 (relative Frobenius step) */
+} ovl_sign_params;
+
+typedef struct {
+    int    status;        /* per-solve OVL_* code */
+    int    k_used;        /* Krylov depth reached (< k on an exact invariant subspace) */
+    int    m_used;        /* deflated vectors */
+    int    newton_iters;  /* scaled Newton iterations for sgn of the small matrix */
+    double beta;          /* |x_perp| or |x_minus|: norm of the Krylov start vector */
+    double beta_k;        /* H_{k+1,k}, the last Arnoldi residual norm */
+} ovl_sign_info;
+
+/* ---- lattice and links ------------------------------------------------ */
+
+/* Create a lattice of dims {Lx,Ly,Lz,Lt} (each >= 2) on the current CUDA
+ * device. antiperiodic_t != 0 flips the sign of hops across the t boundary
+ * (the paper states no boundary condition; periodic is the default).
+ * stream: a cudaStream_t (NULL = legacy default stream). */
+int ovl_create_lattice(const int dims[4], int antiperiodic_t, void* stream, ovl_lattice* out);
+int ovl_destroy_lattice(ovl_lattice lat);
+
+/* Upload SU(3) links U_{n,nu} of Eq. 2 in the canonical layout. Builds the
+ * FP64, FP32 and 12-real (rows 0 and 1; row 2 = conj(row0 x row1)) copies. */
+int ovl_set_links(ovl_lattice lat, const double* U);
+
+/* ---- the operator (Sec. 1, Eq. 2): y = H_w(mu) x = gamma_5 D_w(mu) x ---- */
+
+/* nrhs right-hand sides, canonical layout, stride 24*V doubles between them.
+ * links: OVL_LINKS_* selects the stencil arithmetic (F64: FP64; F32/R12: FP32). */
+int ovl_apply_Hw(ovl_lattice lat, double mu, double m_w, const double* in, double* out,
+                 int nrhs, int links);
+
+/* Stencil on packed spinors (the library's internal site order), for timing
+ * the stencil alone. in/out: device pointers, nrhs vectors of 12*V complex in
+ * format fmt (OVL_VEC_*); mu: nrhs chemical potentials (host array).
+ * fmt F64 requires links F64; fmt F32 takes F32 or R12 links. */
+int ovl_apply_Hw_packed(ovl_lattice lat, const double* mu, double m_w, const void* in,
+                        void* out, int nrhs, int fmt, int links);
+/* Canonical complex128 <-> packed format (device or host canonical side;
+ * packed side must be device memory). */
+int ovl_pack_spinor(ovl_lattice lat, const double* canon, void* packed, int nrhs, int fmt);
+int ovl_unpack_spinor(ovl_lattice lat, const void* packed, double* canon, int nrhs, int fmt);
+
+/* ---- deflation data (Sec. 3 Eq. 13; Sec. 4 Eq. 20) --------------------- */
+
+/* Import m critical eigenvectors computed elsewhere.
+ *  scheme OVL_DEFL_SCHUR: S_or_R = S_m, m orthonormal Schur vectors (m
+ *    canonical spinors, one after another); T = T_m, m x m complex128
+ *    column-major with A S_m = S_m T_m (upper triangular per Eq. 13; any T
+ *    satisfying the relation is accepted); L must be NULL.
+ *  scheme OVL_DEFL_LR: S_or_R = R_m right eigenvectors, T = Lambda_m (m
+ *    complex128 eigenvalues), L = L_m left eigenvectors with L^dag R = I.
+ * mu and m_w record the operator the vectors belong to; ovl_sign_apply
+ * rejects a solve whose mu/m_w differ. */
+int ovl_set_deflation(ovl_lattice lat, double mu, double m_w, int scheme, int m,
+                      const double* S_or_R, const double* T, const double* L,
+                      ovl_deflation* out);
+
+/* Compute the m critical eigenpairs (smallest |Re lambda|, Sec. 5) on the GPU
+ * by restarted Arnoldi (Krylov-Schur) on the same stencil and Gram-Schmidt
+ * kernels, and build the deflation data for the scheme. tol: relative
+ * residual |A r - lambda r| / (|A|_est |r|) required for every pair;
+ * max_restarts bounds the work (OVL_ENOCONV past it). */
+int ovl_deflation_setup(ovl_lattice lat, double mu, double m_w, int scheme, int m,
+                        double tol, int max_restarts, ovl_deflation* out);
+
+/* Copy the deflation data back (canonical layouts as in ovl_set_deflation;
+ * L ignored for Schur). Host or device pointers. */
+int ovl_get_deflation(ovl_deflation d, int* scheme, int* m, double* S_or_R, double* T, double* L);
+int ovl_destroy_deflation(ovl_deflation d);
+
+/* ---- the sign function (Secs. 2-4) ------------------------------------- */
+
+/* nsolve independent approximations y_i ~ sgn(H_w(mu_i)) b_i run together
+ * (one launch per step for the whole batch; uneven k allowed).
+ *  params[i]: mu, m_w, k, precision of solve i.
+ *  defl[i]:   deflation data for solve i or NULL (no deflation, Eq. 11);
+ *             Schur -> Eq. 19 (computed as Eq. 16 on the block matrix),
+ *             LR    -> Eq. 22.  defl may itself be NULL (no solve deflated).
+ *  b, y:      nsolve canonical spinors each (stride 24*V doubles).
+ *  info:      nsolve records, or NULL.
+ * Returns the first non-zero per-solve status (all solves are attempted). */
+int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params* params,
+                   const ovl_deflation* defl, const double* b, double* y, ovl_sign_info* info);
+
+/* Message for the last failed call on this handle (NULL handle: the last
+ * failure of a call that had no handle yet, e.g. ovl_create_lattice). */
+const char* ovl_last_error(ovl_lattice lat);
+
+/* Version string of the build ("ovl <semver> sm_103a"). */
+const char* ovl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OVL_H */

@@ -1,0 +1,102 @@
+// Double-float ("df") arithmetic: a value is an unevaluated sum hi + lo of two
+// FP32 numbers (about 48 significant bits). GB300 issues FP32 at 64 times its
+// FP64 rate, so FP64-class accumulations here run on the FP32 pipes with the
+// error-free transformations of Dekker (1971) and Knuth (TAOCP vol. 2):
+//   two_sum(a, b)  : s + e == a + b exactly      (6 flops, no ordering needed)
+//   fast_two_sum   : same when |a| >= |b|        (3 flops)
+//   two_prod(a, b) : p + e == a * b exactly      (1 mul + 1 fma)
+// The *_rn intrinsics stop the compiler from contracting these steps into
+// fused operations, which would break exactness.
+#pragma once
+#include <cuda_runtime.h>
+
+struct dfc {  // complex df: (re_hi, im_hi) + (re_lo, im_lo)
+    float2 hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// split an FP64 value into hi + lo FP32 (exact to 48 bits)
+__host__ __device__ __forceinline__ float2 split_d(double x) {
+    float h = (float)x;
+    float l = (float)(x - (double)h);
+    return make_float2(h, l);
+}
+__device__ __forceinline__ dfc dfc_from(double2 z) {
+    float2 a = split_d(z.x), b = split_d(z.y);
+    dfc r;
+    r.hi = make_float2(a.x, b.x);
+    r.lo = make_float2(a.y, b.y);
+    return r;
+}
+__device__ __forceinline__ double2 dfc_to(const dfc& z) {
+    return make_double2((double)z.hi.x + (double)z.lo.x, (double)z.hi.y + (double)z.lo.y);
+}
+
+// Accumulator for sum_k q_k * g_k with q, g df complex.
+// hi parts are carried with two_sum; every rounding error and every cross
+// term (hi*lo, lo*hi) goes into the lo accumulator with plain FP32 FMAs
+// (their relative size is 2^-24, so FP32 rounding of them costs 2^-48).
+struct dfacc {
+    float2 s;  // hi sum
+    float2 t;  // low-order terms
+};
+__device__ __forceinline__ void dfacc_zero(dfacc& a) {
+    a.s = make_float2(0.f, 0.f);
+    a.t = make_float2(0.f, 0.f);
+}
+// a += q * g (complex), q = qh + ql, g = gh + gl
+__device__ __forceinline__ void dfacc_mac(dfacc& a, float2 qh, float2 ql, float2 gh, float2 gl) {
+    float p, e, s, err;
+    // real part: qh.x*gh.x - qh.y*gh.y
+    two_prod(qh.x, gh.x, p, e);
+    two_sum(a.s.x, p, s, err);
+    a.s.x = s;
+    a.t.x = __fadd_rn(a.t.x, __fadd_rn(err, e));
+    two_prod(-qh.y, gh.y, p, e);
+    two_sum(a.s.x, p, s, err);
+    a.s.x = s;
+    a.t.x = __fadd_rn(a.t.x, __fadd_rn(err, e));
+    a.t.x = fmaf(qh.x, gl.x, a.t.x);
+    a.t.x = fmaf(-qh.y, gl.y, a.t.x);
+    a.t.x = fmaf(ql.x, gh.x, a.t.x);
+    a.t.x = fmaf(-ql.y, gh.y, a.t.x);
+    // imag part: qh.x*gh.y + qh.y*gh.x
+    two_prod(qh.x, gh.y, p, e);
+    two_sum(a.s.y, p, s, err);
+    a.s.y = s;
+    a.t.y = __fadd_rn(a.t.y, __fadd_rn(err, e));
+    two_prod(qh.y, gh.x, p, e);
+    two_sum(a.s.y, p, s, err);
+    a.s.y = s;
+    a.t.y = __fadd_rn(a.t.y, __fadd_rn(err, e));
+    a.t.y = fmaf(qh.x, gl.y, a.t.y);
+    a.t.y = fmaf(qh.y, gl.x, a.t.y);
+    a.t.y = fmaf(ql.x, gh.y, a.t.y);
+    a.t.y = fmaf(ql.y, gh.x, a.t.y);
+}
+// merge b into a (both accumulators)
+__device__ __forceinline__ void dfacc_add(dfacc& a, const dfacc& b) {
+    float s, err;
+    two_sum(a.s.x, b.s.x, s, err);
+    a.s.x = s;
+    a.t.x = __fadd_rn(a.t.x, __fadd_rn(err, b.t.x));
+    two_sum(a.s.y, b.s.y, s, err);
+    a.s.y = s;
+    a.t.y = __fadd_rn(a.t.y, __fadd_rn(err, b.t.y));
+}
+__device__ __forceinline__ double2 dfacc_value(const dfacc& a) {
+    return make_double2((double)a.s.x + (double)a.t.x, (double)a.s.y + (double)a.t.y);
+}

@@ -1,0 +1,697 @@
+// Streaming Gram-Schmidt kernels of the Arnoldi step (Sec. 2, Eq. 7) and of
+// the augmented Arnoldi step of the Schur deflation (Sec. 3, Eq. 14).
+//
+// Classical Gram-Schmidt with one reorthogonalisation is organised as the
+// "delayed" variant: step j makes two passes over the basis Q_p (p = m + j - 1
+// final columns) instead of four:
+//   pass A (k_gs_dot):    a = Q_p^dag u_j,  b = Q_p^dag w    (w = A u_j)
+//   small  (k_gs_small):  nu = sqrt(|u_j|^2 - |a|^2); q_{p+1} = (u_j - Q_p a)/nu
+//                         is the reorthogonalised, normalised column; the
+//                         coefficients c of A q_{p+1} on Q_{p+1} follow from
+//                         a, b and d = H a without touching Q again
+//   pass B (k_gs_update): q_{p+1} = u_j/nu - Q_p (a/nu)        -> column p of Q
+//                         u_{j+1} = w/nu - (e_p/nu) u_j - Q_p g -> next candidate
+// By construction A q_{p+1} = Q_{p+1} c + u_{j+1} holds to the accuracy of the
+// pass-B arithmetic for whatever coefficients are used, so the inner products
+// of pass A only need FP32 products (they steer orthogonality), while pass B
+// accumulates in double-float (48 bits) against the stored hi+lo basis.
+#include "df.cuh"
+#include "krylov.cuh"
+
+namespace {
+
+constexpr int DOT_THREADS = 256;
+constexpr int DOT_RPL = 8;                      // rows per lane (4 float4 = 8 complex)
+constexpr int DOT_RB = 32 * DOT_RPL;            // rows per block iteration
+constexpr int UPD_RPL = 4;
+constexpr int UPD_RB = 32 * UPD_RPL;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sumd(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int solve_p(const SolveDev& d, int j) { return j < 0 ? d.m_q + d.k_used : d.m_q + j - 1; }
+__device__ __forceinline__ bool solve_in_step(const SolveDev& d, int j) {
+    if (!d.active) return false;
+    return j < 0 ? true : j <= d.k;
+}
+
+// ---------------------------------------------------------------------------
+// pass A: a = Q_p^dag u, b = Q_p^dag w and the scalars |u|^2, u^dag w, |w|^2
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(DOT_THREADS) k_gs_dot(BatchDev B, int j) {
+    const int s = blockIdx.y;
+    const SolveDev& d = B.sd[s];
+    if (!solve_in_step(d, j)) return;
+    const int p = solve_p(d, j);
+    const size_t N = B.N;
+    __shared__ double2 acc[2 * OVL_MAXCOL + 3];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int o = tid; o < 2 * p + 3; o += DOT_THREADS) acc[o] = make_double2(0.0, 0.0);
+    __syncthreads();
+    const double2* __restrict__ u = d.u;
+    const double2* __restrict__ w = d.w;
+    for (size_t base = (size_t)blockIdx.x * DOT_RB; base < N; base += (size_t)gridDim.x * DOT_RB) {
+        float2 uf[DOT_RPL], wf[DOT_RPL];
+#pragma unroll
+        for (int i = 0; i < DOT_RPL / 2; i++) {
+            size_t r = base + 64 * i + 2 * lane;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                if (r + h < N) {
+                    double2 a = u[r + h], b = w[r + h];
+                    uf[2 * i + h] = make_float2((float)a.x, (float)a.y);
+                    wf[2 * i + h] = make_float2((float)b.x, (float)b.y);
+                } else {
+                    uf[2 * i + h] = make_float2(0.f, 0.f);
+                    wf[2 * i + h] = make_float2(0.f, 0.f);
+                }
+            }
+        }
+        if (warp == 0) {
+            float guu = 0.f, guwr = 0.f, guwi = 0.f, gww = 0.f;
+#pragma unroll
+            for (int i = 0; i < DOT_RPL; i++) {
+                guu = fmaf(uf[i].x, uf[i].x, fmaf(uf[i].y, uf[i].y, guu));
+                gww = fmaf(wf[i].x, wf[i].x, fmaf(wf[i].y, wf[i].y, gww));
+                guwr = fmaf(uf[i].x, wf[i].x, fmaf(uf[i].y, wf[i].y, guwr));
+                guwi = fmaf(uf[i].x, wf[i].y, fmaf(-uf[i].y, wf[i].x, guwi));
+            }
+            guu = warp_sum(guu);
+            gww = warp_sum(gww);
+            guwr = warp_sum(guwr);
+            guwi = warp_sum(guwi);
+            if (lane == 0) {
+                acc[2 * p].x += guu;
+                acc[2 * p + 1].x += guwr;
+                acc[2 * p + 1].y += guwi;
+                acc[2 * p + 2].x += gww;
+            }
+        }
+        const bool full = base + DOT_RB <= N;
+        for (int c = warp; c < p; c += DOT_THREADS / 32) {
+            const float4* __restrict__ q = (const float4*)d.qhi[c];
+            float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+#pragma unroll
+            for (int i = 0; i < DOT_RPL / 2; i++) {
+                size_t r = base + 64 * i + 2 * lane;  // even, pairs (r, r+1)
+                float4 qq = (full || r < N) ? __ldg(q + (r >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                // conj(q) * u
+                ar = fmaf(qq.x, uf[2 * i].x, fmaf(qq.y, uf[2 * i].y, ar));
+                ai = fmaf(qq.x, uf[2 * i].y, fmaf(-qq.y, uf[2 * i].x, ai));
+                ar = fmaf(qq.z, uf[2 * i + 1].x, fmaf(qq.w, uf[2 * i + 1].y, ar));
+                ai = fmaf(qq.z, uf[2 * i + 1].y, fmaf(-qq.w, uf[2 * i + 1].x, ai));
+                br = fmaf(qq.x, wf[2 * i].x, fmaf(qq.y, wf[2 * i].y, br));
+                bi = fmaf(qq.x, wf[2 * i].y, fmaf(-qq.y, wf[2 * i].x, bi));
+                br = fmaf(qq.z, wf[2 * i + 1].x, fmaf(qq.w, wf[2 * i + 1].y, br));
+                bi = fmaf(qq.z, wf[2 * i + 1].y, fmaf(-qq.w, wf[2 * i + 1].x, bi));
+            }
+            ar = warp_sum(ar);
+            ai = warp_sum(ai);
+            br = warp_sum(br);
+            bi = warp_sum(bi);
+            if (lane == 0) {
+                acc[c].x += ar;
+                acc[c].y += ai;
+                acc[p + c].x += br;
+                acc[p + c].y += bi;
+            }
+        }
+    }
+    __syncthreads();
+    double2* out = B.part + ((size_t)s * B.G + blockIdx.x) * B.pstride;
+    for (int o = tid; o < 2 * p + 3; o += DOT_THREADS) out[o] = acc[o];
+}
+
+// sum the per-block partials: dots[s][o] = sum_g part[s][g][o]
+__global__ void __launch_bounds__(256) k_gs_reduce(BatchDev B, int j, int G_used) {
+    const int s = blockIdx.y;
+    const SolveDev& d = B.sd[s];
+    if (!solve_in_step(d, j)) return;
+    const int p = solve_p(d, j);
+    const int nout = 2 * p + 3;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int o = blockIdx.x * 32 + lane;
+    __shared__ double2 red[8][32];
+    double2 v = make_double2(0.0, 0.0);
+    if (o < nout)
+        for (int g = warp; g < G_used; g += 8) {
+            double2 t = B.part[((size_t)s * B.G + g) * B.pstride + o];
+            v.x += t.x;
+            v.y += t.y;
+        }
+    red[warp][lane] = v;
+    __syncthreads();
+    if (warp == 0 && o < nout) {
+        double2 t = red[0][lane];
+        for (int k = 1; k < 8; k++) {
+            t.x += red[k][lane].x;
+            t.y += red[k][lane].y;
+        }
+        d.dots[o] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// small step: d = H a (FP32 is enough: |a| is at the rounding level of one
+// Gram-Schmidt pass), then nu, c, e and the pass-B coefficients; H update.
+// j < 0: final pass after the last step (only the H update of column p-1).
+// ---------------------------------------------------------------------------
+constexpr int SM_ROWS = 64;
+
+__global__ void __launch_bounds__(256) k_gs_small(BatchDev B, int j) {
+    const int s = blockIdx.y;
+    SolveDev& d = B.sd[s];
+    if (!solve_in_step(d, j)) return;
+    const int p = solve_p(d, j);
+    const int ld = d.ldH;
+    const bool first = (j == 1);
+    const bool final_pass = (j < 0);
+    __shared__ float2 a32[OVL_MAXCOL];
+    __shared__ float2 red[4][SM_ROWS];
+    __shared__ int is_last;
+    const int tid = threadIdx.x;
+    const double2* dots = d.dots;
+    // phase 1: rows of d (not needed for the first step or the final pass)
+    if (!first && !final_pass) {
+        for (int c = tid; c < p; c += 256) a32[c] = make_float2((float)dots[c].x, (float)dots[c].y);
+        __syncthreads();
+        const int row = blockIdx.x * SM_ROWS + (tid & (SM_ROWS - 1));
+        const int cg = tid / SM_ROWS;  // 0..3
+        float2 acc = make_float2(0.f, 0.f);
+        if (row < p) {
+            // H is upper Hessenberg below the Schur block: row i has no entries left of column i-1
+            int c0 = row >= d.m_q + 1 ? row - 1 : 0;
+            for (int c = c0 + cg; c < p; c += 4) {
+                float2 h = d.H32[row + (size_t)c * ld];
+                float2 av = a32[c];
+                acc.x = fmaf(h.x, av.x, fmaf(-h.y, av.y, acc.x));
+                acc.y = fmaf(h.x, av.y, fmaf(h.y, av.x, acc.y));
+            }
+        }
+        red[cg][tid & (SM_ROWS - 1)] = acc;
+        __syncthreads();
+        if (tid < SM_ROWS && row < p) {
+            float2 t = red[0][tid];
+            for (int k = 1; k < 4; k++) {
+                t.x += red[k][tid].x;
+                t.y += red[k][tid].y;
+            }
+            d.dvec[row] = make_double2(t.x, t.y);
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) is_last = (atomicAdd(&B.counters[s], 1) == (int)gridDim.x - 1);
+        __syncthreads();
+        if (!is_last) return;
+        __threadfence();
+    } else if (blockIdx.x != 0) {
+        return;
+    }
+    // phase 2: one block per solve
+    __shared__ double sh_r[8];
+    __shared__ double2 sh_c[8];
+    __shared__ double sh_nu, sh_ep_r, sh_ep_i;
+    __shared__ int sh_stop;
+    const int lane = tid & 31, warp = tid >> 5;
+    // |a|^2 and a^dag b
+    double aa = 0.0;
+    double2 ab = make_double2(0.0, 0.0);
+    if (!first)
+        for (int c = tid; c < p; c += 256) {
+            double2 av = dots[c], bv = dots[p + c];
+            aa += av.x * av.x + av.y * av.y;
+            ab.x += av.x * bv.x + av.y * bv.y;
+            ab.y += av.x * bv.y - av.y * bv.x;
+        }
+    aa = warp_sumd(aa);
+    ab.x = warp_sumd(ab.x);
+    ab.y = warp_sumd(ab.y);
+    if (lane == 0) {
+        sh_r[warp] = aa;
+        sh_c[warp] = ab;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double A2 = 0.0;
+        double2 AB = make_double2(0.0, 0.0);
+        for (int k = 0; k < 8; k++) {
+            A2 += sh_r[k];
+            AB.x += sh_c[k].x;
+            AB.y += sh_c[k].y;
+        }
+        double guu = dots[2 * p].x;
+        double nu2 = first ? 1.0 : guu - A2;
+        int stop = 0;
+        if (!(nu2 == nu2) || !(guu == guu)) {
+            stop = 2;  // NaN
+        } else if (!first && nu2 <= 1e-24 * guu) {
+            stop = 1;  // invariant subspace reached (happy breakdown)
+            nu2 = 0.0;
+        }
+        double nu = sqrt(nu2 > 0.0 ? nu2 : 0.0);
+        sh_nu = nu;
+        sh_stop = stop;
+        if (!final_pass && !stop) {
+            // q^dag w = (u^dag w - a^dag b)/nu, and d_p = nu a_{p-1}
+            double2 guw = dots[2 * p + 1];
+            double2 qw = make_double2((guw.x - AB.x) / nu, (guw.y - AB.y) / nu);
+            double2 dp = make_double2(0.0, 0.0);
+            if (!first) {
+                double2 al = dots[p - 1];
+                dp = make_double2(nu * al.x, nu * al.y);
+            }
+            d.dvec[p] = dp;
+            double2 cp = make_double2((qw.x - dp.x) / nu, (qw.y - dp.y) / nu);
+            double2 ep = make_double2(dp.x / nu + cp.x, dp.y / nu + cp.y);
+            d.H[p + (size_t)p * ld] = cp;
+            d.H32[p + (size_t)p * ld] = make_float2((float)cp.x, (float)cp.y);
+            sh_ep_r = ep.x;
+            sh_ep_i = ep.y;
+            d.scal[0] = 1.0 / nu;
+            d.scal[1] = -ep.x / nu;
+            d.scal[2] = -ep.y / nu;
+            d.scal[3] = nu;
+        }
+    }
+    __syncthreads();
+    const double nu = sh_nu;
+    const int stop = sh_stop;
+    // update column p-1 with the reorthogonalisation coefficients and nu
+    if (!first) {
+        for (int c = tid; c < p; c += 256) {
+            double2 av = dots[c];
+            double2 h = d.H[c + (size_t)(p - 1) * ld];
+            h.x += av.x;
+            h.y += av.y;
+            d.H[c + (size_t)(p - 1) * ld] = h;
+            d.H32[c + (size_t)(p - 1) * ld] = make_float2((float)h.x, (float)h.y);
+        }
+        if (tid == 0) {
+            d.H[p + (size_t)(p - 1) * ld] = make_double2(nu, 0.0);
+            d.H32[p + (size_t)(p - 1) * ld] = make_float2((float)nu, 0.f);
+        }
+    }
+    if (final_pass || stop) {
+        if (tid == 0) {
+            d.scal[4] = nu;
+            if (stop == 2) {
+                d.status = OVL_ENOCONV;
+                d.active = 0;
+            } else if (stop == 1) {
+                d.k_used = j - 1;  // the space spanned so far is invariant
+                d.active = 0;
+                d.scal[4] = 0.0;
+            }
+            if (final_pass) d.active = 0;
+        }
+        if (!final_pass && tid == 0) B.counters[s] = 0;
+        return;
+    }
+    // coefficients of column p (rows 0..p-1) and of pass B
+    const double inv_nu = 1.0 / nu;
+    const double epr = sh_ep_r, epi = sh_ep_i;
+    for (int c = tid; c < p; c += 256) {
+        double2 av = first ? make_double2(0.0, 0.0) : dots[c];
+        double2 bv = dots[p + c];
+        double2 dv = first ? make_double2(0.0, 0.0) : d.dvec[c];
+        double2 cc = make_double2((bv.x - dv.x) * inv_nu, (bv.y - dv.y) * inv_nu);
+        d.H[c + (size_t)p * ld] = cc;
+        d.H32[c + (size_t)p * ld] = make_float2((float)cc.x, (float)cc.y);
+        double2 e = make_double2(dv.x * inv_nu + cc.x, dv.y * inv_nu + cc.y);
+        // g = e - (e_p/nu) a
+        double2 g = make_double2(e.x - (epr * av.x - epi * av.y) * inv_nu, e.y - (epr * av.y + epi * av.x) * inv_nu);
+        d.ap[c] = make_float2((float)(av.x * inv_nu), (float)(av.y * inv_nu));
+        float2 sx = split_d(g.x), sy = split_d(g.y);
+        d.gh[c] = make_float2(sx.x, sy.x);
+        d.gl[c] = make_float2(sx.y, sy.y);
+    }
+    if (tid == 0) B.counters[s] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// pass B: q_{p+1} and u_{j+1} (see the file header)
+// ---------------------------------------------------------------------------
+template <bool DF>
+__global__ void __launch_bounds__(256) k_gs_update(BatchDev B, int j) {
+    const int s = blockIdx.y;
+    const SolveDev& d = B.sd[s];
+    if (!solve_in_step(d, j)) return;
+    const int p = solve_p(d, j);
+    const size_t N = B.N;
+    __shared__ float2 s_ap[OVL_MAXCOL];
+    __shared__ float2 s_gh[OVL_MAXCOL];
+    __shared__ float2 s_gl[OVL_MAXCOL];
+    __shared__ float4 red_q[8][UPD_RB / 2];   // sq for row pairs
+    __shared__ float4 red_g[8][UPD_RB];       // (s.x, s.y, t.x, t.y) per row
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int c = tid; c < p; c += 256) {
+        s_ap[c] = d.ap[c];
+        s_gh[c] = d.gh[c];
+        if (DF) s_gl[c] = d.gl[c];
+    }
+    const double inv_nu = d.scal[0];
+    const double2 cu = make_double2(d.scal[1], d.scal[2]);
+    float2* qh_out = (float2*)d.qhi[p];
+    float2* ql_out = DF ? (float2*)d.qlo[p] : nullptr;
+    __syncthreads();
+    for (size_t base = (size_t)blockIdx.x * UPD_RB; base < N; base += (size_t)gridDim.x * UPD_RB) {
+        const bool full = base + UPD_RB <= N;
+        float2 sq[UPD_RPL];
+        dfacc sg[UPD_RPL];
+#pragma unroll
+        for (int i = 0; i < UPD_RPL; i++) {
+            sq[i] = make_float2(0.f, 0.f);
+            dfacc_zero(sg[i]);
+        }
+        for (int c = warp; c < p; c += 8) {
+            const float4* __restrict__ qh = (const float4*)d.qhi[c];
+            const float4* __restrict__ ql = DF ? (const float4*)d.qlo[c] : nullptr;
+            const float2 apc = s_ap[c], ghc = s_gh[c];
+            const float2 glc = DF ? s_gl[c] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < UPD_RPL / 2; i++) {
+                size_t r = base + 64 * i + 2 * lane;
+                bool ok = full || r < N;
+                float4 h4 = ok ? __ldg(qh + (r >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 l4 = (DF && ok) ? __ldg(ql + (r >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                float2 h0 = make_float2(h4.x, h4.y), h1 = make_float2(h4.z, h4.w);
+                float2 l0 = make_float2(l4.x, l4.y), l1 = make_float2(l4.z, l4.w);
+                // sq += q * ap   (FP32; |ap| is tiny)
+                sq[2 * i].x = fmaf(h0.x, apc.x, fmaf(-h0.y, apc.y, sq[2 * i].x));
+                sq[2 * i].y = fmaf(h0.x, apc.y, fmaf(h0.y, apc.x, sq[2 * i].y));
+                sq[2 * i + 1].x = fmaf(h1.x, apc.x, fmaf(-h1.y, apc.y, sq[2 * i + 1].x));
+                sq[2 * i + 1].y = fmaf(h1.x, apc.y, fmaf(h1.y, apc.x, sq[2 * i + 1].y));
+                if (DF) {
+                    dfacc_mac(sg[2 * i], h0, l0, ghc, glc);
+                    dfacc_mac(sg[2 * i + 1], h1, l1, ghc, glc);
+                } else {
+                    sg[2 * i].s.x = fmaf(h0.x, ghc.x, fmaf(-h0.y, ghc.y, sg[2 * i].s.x));
+                    sg[2 * i].s.y = fmaf(h0.x, ghc.y, fmaf(h0.y, ghc.x, sg[2 * i].s.y));
+                    sg[2 * i + 1].s.x = fmaf(h1.x, ghc.x, fmaf(-h1.y, ghc.y, sg[2 * i + 1].s.x));
+                    sg[2 * i + 1].s.y = fmaf(h1.x, ghc.y, fmaf(h1.y, ghc.x, sg[2 * i + 1].s.y));
+                }
+            }
+        }
+        // cross-warp reduction
+#pragma unroll
+        for (int i = 0; i < UPD_RPL / 2; i++) {
+            int rr = 64 * i + 2 * lane;  // local row (even)
+            red_q[warp][rr >> 1] = make_float4(sq[2 * i].x, sq[2 * i].y, sq[2 * i + 1].x, sq[2 * i + 1].y);
+            red_g[warp][rr] = make_float4(sg[2 * i].s.x, sg[2 * i].s.y, sg[2 * i].t.x, sg[2 * i].t.y);
+            red_g[warp][rr + 1] =
+                make_float4(sg[2 * i + 1].s.x, sg[2 * i + 1].s.y, sg[2 * i + 1].t.x, sg[2 * i + 1].t.y);
+        }
+        __syncthreads();
+        if (tid < UPD_RB) {
+            const int rr = tid;
+            const size_t r = base + rr;
+            if (r < N) {
+                float2 tq = make_float2(0.f, 0.f);
+                dfacc tg;
+                dfacc_zero(tg);
+                for (int k = 0; k < 8; k++) {
+                    float4 q4 = red_q[k][rr >> 1];
+                    tq.x += (rr & 1) ? q4.z : q4.x;
+                    tq.y += (rr & 1) ? q4.w : q4.y;
+                    float4 g4 = red_g[k][rr];
+                    dfacc t;
+                    t.s = make_float2(g4.x, g4.y);
+                    t.t = make_float2(g4.z, g4.w);
+                    dfacc_add(tg, t);
+                }
+                double2 ur = d.u[r], wr = d.w[r];
+                double2 sgv = dfacc_value(tg);
+                double2 q = make_double2(ur.x * inv_nu - (double)tq.x, ur.y * inv_nu - (double)tq.y);
+                double2 un = make_double2(wr.x * inv_nu + (cu.x * ur.x - cu.y * ur.y) - sgv.x,
+                                          wr.y * inv_nu + (cu.x * ur.y + cu.y * ur.x) - sgv.y);
+                float2 qx = split_d(q.x), qy = split_d(q.y);
+                qh_out[r] = make_float2(qx.x, qy.x);
+                if (DF) ql_out[r] = make_float2(qx.y, qy.y);
+                d.u[r] = un;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// accurate projections (FP64) for deflation and start vectors
+// ---------------------------------------------------------------------------
+constexpr int PJ_RPL = 4;
+constexpr int PJ_RB = 32 * PJ_RPL;
+
+__global__ void __launch_bounds__(256) k_proj_dot(ProjDev* pds, double2* part, int G, int pstride, size_t N) {
+    const int s = blockIdx.y;
+    const ProjDev d = pds[s];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ double2 acc[OVL_MAXCOL + 1];
+    for (int o = tid; o <= d.ncol; o += 256) acc[o] = make_double2(0.0, 0.0);
+    __syncthreads();
+    for (size_t base = (size_t)blockIdx.x * PJ_RB; base < N; base += (size_t)gridDim.x * PJ_RB) {
+        double2 xv[PJ_RPL];
+#pragma unroll
+        for (int i = 0; i < PJ_RPL; i++) {
+            size_t r = base + 32 * i + lane;
+            xv[i] = r < N ? d.x[r] : make_double2(0.0, 0.0);
+        }
+        if (warp == 0) {
+            double nn = 0.0;
+#pragma unroll
+            for (int i = 0; i < PJ_RPL; i++) nn += xv[i].x * xv[i].x + xv[i].y * xv[i].y;
+            nn = warp_sumd(nn);
+            if (lane == 0) acc[d.ncol].x += nn;
+        }
+        for (int c = warp; c < d.ncol; c += 8) {
+            const float2* qh = d.qhi[c];
+            const float2* ql = d.qlo[c];
+            double ar = 0.0, ai = 0.0;
+#pragma unroll
+            for (int i = 0; i < PJ_RPL; i++) {
+                size_t r = base + 32 * i + lane;
+                if (r < N) {
+                    float2 h = qh[r], l = ql[r];
+                    double qr = (double)h.x + (double)l.x, qi = (double)h.y + (double)l.y;
+                    ar += qr * xv[i].x + qi * xv[i].y;
+                    ai += qr * xv[i].y - qi * xv[i].x;
+                }
+            }
+            ar = warp_sumd(ar);
+            ai = warp_sumd(ai);
+            if (lane == 0) {
+                acc[c].x += ar;
+                acc[c].y += ai;
+            }
+        }
+    }
+    __syncthreads();
+    double2* out = part + ((size_t)s * G + blockIdx.x) * pstride;
+    for (int o = tid; o <= d.ncol; o += 256) out[o] = acc[o];
+}
+
+__global__ void __launch_bounds__(256) k_proj_reduce(ProjDev* pds, const double2* part, int G, int pstride) {
+    const int s = blockIdx.y;
+    const ProjDev d = pds[s];
+    const int nout = d.ncol + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int o = blockIdx.x * 32 + lane;
+    __shared__ double2 red[8][32];
+    double2 v = make_double2(0.0, 0.0);
+    if (o < nout)
+        for (int g = warp; g < G; g += 8) {
+            double2 t = part[((size_t)s * G + g) * pstride + o];
+            v.x += t.x;
+            v.y += t.y;
+        }
+    red[warp][lane] = v;
+    __syncthreads();
+    if (warp == 0 && o < nout) {
+        double2 t = red[0][lane];
+        for (int k = 1; k < 8; k++) {
+            t.x += red[k][lane].x;
+            t.y += red[k][lane].y;
+        }
+        d.out[o] = t;
+    }
+}
+
+// x -= sum_c Q[:,c] coef[c]   (df accumulation, FP64 subtraction)
+__global__ void __launch_bounds__(256) k_proj_update(ProjDev* pds, size_t N) {
+    const int s = blockIdx.y;
+    const ProjDev d = pds[s];
+    __shared__ float2 gh[OVL_MAXCOL], gl[OVL_MAXCOL];
+    for (int c = threadIdx.x; c < d.ncol; c += 256) {
+        double2 g = d.coef[c];
+        float2 a = split_d(g.x), b = split_d(g.y);
+        gh[c] = make_float2(a.x, b.x);
+        gl[c] = make_float2(a.y, b.y);
+    }
+    __syncthreads();
+    for (size_t r = blockIdx.x * (size_t)256 + threadIdx.x; r < N; r += (size_t)gridDim.x * 256) {
+        dfacc acc;
+        dfacc_zero(acc);
+        for (int c = 0; c < d.ncol; c++) dfacc_mac(acc, d.qhi[c][r], d.qlo[c][r], gh[c], gl[c]);
+        double2 v = dfacc_value(acc);
+        double2 x = d.x[r];
+        d.x[r] = make_double2(x.x - v.x, x.y - v.y);
+    }
+}
+
+// y = sum_c Q[:,c] g[c]   (df accumulation)
+__global__ void __launch_bounds__(256) k_gemv(GemvDev* gds, size_t N) {
+    const int s = blockIdx.y;
+    const GemvDev d = gds[s];
+    __shared__ float2 gh[OVL_MAXCOL + 64], gl[OVL_MAXCOL + 64];
+    for (int c = threadIdx.x; c < d.ncol; c += 256) {
+        double2 g = d.g[c];
+        float2 a = split_d(g.x), b = split_d(g.y);
+        gh[c] = make_float2(a.x, b.x);
+        gl[c] = make_float2(a.y, b.y);
+    }
+    __syncthreads();
+    for (size_t r = blockIdx.x * (size_t)256 + threadIdx.x; r < N; r += (size_t)gridDim.x * 256) {
+        dfacc acc;
+        dfacc_zero(acc);
+        for (int c = 0; c < d.ncol; c++) {
+            float2 h = d.qhi[c][r];
+            const float2* lp = d.qlo[c];
+            float2 l = lp ? lp[r] : make_float2(0.f, 0.f);
+            dfacc_mac(acc, h, l, gh[c], gl[c]);
+        }
+        d.y[r] = dfacc_value(acc);
+    }
+}
+
+// start vector: v1 = x/beta into column m_q and u
+template <bool DF>
+__global__ void __launch_bounds__(256) k_start(BatchDev B, const double* beta2, int stride) {
+    const int s = blockIdx.y;
+    SolveDev& d = B.sd[s];
+    if (!d.active) return;
+    double b2 = beta2[(size_t)s * stride];
+    if (!(b2 > 0.0)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            d.active = 0;
+            d.k_used = 0;
+        }
+        return;
+    }
+    double inv = 1.0 / sqrt(b2);
+    float2* qh = (float2*)d.qhi[d.m_q];
+    float2* ql = DF ? (float2*)d.qlo[d.m_q] : nullptr;
+    for (size_t r = blockIdx.x * (size_t)256 + threadIdx.x; r < B.N; r += (size_t)gridDim.x * 256) {
+        double2 x = d.u[r];
+        double2 v = make_double2(x.x * inv, x.y * inv);
+        float2 a = split_d(v.x), b = split_d(v.y);
+        qh[r] = make_float2(a.x, b.x);
+        if (DF) ql[r] = make_float2(a.y, b.y);
+        // u_1 must be the stored 48-bit value in the FP64 mode, the stored FP32 value otherwise
+        d.u[r] = DF ? make_double2((double)a.x + (double)a.y, (double)b.x + (double)b.y) : make_double2(a.x, b.x);
+    }
+}
+
+}  // namespace
+
+int ovl_gs_grid(ovl_lattice lat) {
+    size_t blocks = (lat->N + DOT_RB - 1) / DOT_RB;
+    size_t g = (size_t)lat->num_sms * 2;
+    if (blocks < g) g = blocks;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+int ovl_gs_dot(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
+    dim3 grid(b.G, b.nsolve);
+    k_gs_dot<<<grid, DOT_THREADS, 0, st>>>(b, j);
+    OVL_LAUNCH_CHECK(lat);
+    return OVL_OK;
+}
+
+int ovl_gs_reduce(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
+    int maxout = 2 * b.pmax + 3;
+    dim3 grid((maxout + 31) / 32, b.nsolve);
+    k_gs_reduce<<<grid, 256, 0, st>>>(b, j, b.G);
+    OVL_LAUNCH_CHECK(lat);
+    return OVL_OK;
+}
+
+int ovl_gs_small(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
+    // enough blocks for the longest solve (p < OVL_MAXCOL)
+    dim3 grid(j == 1 || j < 0 ? 1 : (b.pmax + SM_ROWS - 1) / SM_ROWS, b.nsolve);
+    k_gs_small<<<grid, 256, 0, st>>>(b, j);
+    OVL_LAUNCH_CHECK(lat);
+    return OVL_OK;
+}
+
+int ovl_gs_update(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
+    size_t blocks = (b.N + UPD_RB - 1) / UPD_RB;
+    size_t g = (size_t)lat->num_sms * 4;
+    if (blocks < g) g = blocks;
+    dim3 grid((unsigned)g, b.nsolve);
+    // the batch is homogeneous in precision (checked by the caller)
+    if (b.df)
+        k_gs_update<true><<<grid, 256, 0, st>>>(b, j);
+    else
+        k_gs_update<false><<<grid, 256, 0, st>>>(b, j);
+    OVL_LAUNCH_CHECK(lat);
+    return OVL_OK;
+}
+
+int ovl_gs_final(ovl_lattice lat, const BatchDev& b, cudaStream_t st) {
+    if (int rc = ovl_gs_dot(lat, b, -1, st)) return rc;
+    if (int rc = ovl_gs_reduce(lat, b, -1, st)) return rc;
+    return ovl_gs_small(lat, b, -1, st);
+}
+
+int ovl_proj_dot(ovl_lattice lat, ProjDev* pd_dev, int nsolve, int maxcol, double2* part, int G, cudaStream_t st) {
+    int pstride = maxcol + 1;
+    dim3 grid(G, nsolve);
+    k_proj_dot<<<grid, 256, 0, st>>>(pd_dev, part, G, pstride, lat->N);
+    OVL_LAUNCH_CHECK(lat);
+    dim3 g2((maxcol + 1 + 31) / 32, nsolve);
+    k_proj_reduce<<<g2, 256, 0, st>>>(pd_dev, part, G, pstride);
+    OVL_LAUNCH_CHECK(lat);
+    return OVL_OK;
+}
+
+int ovl_proj_update(ovl_lattice lat, ProjDev* pd_dev, int nsolve, int maxcol, cudaStream_t st) {
+    (void)maxcol;
+    size_t blocks = (lat->N + 255) / 256;
+    size_t g = (size_t)lat->num_sms * 4;
+    if (blocks < g) g = blocks;
+    dim3 grid((unsigned)g, nsolve);
+    k_proj_update<<<grid, 256, 0, st>>>(pd_dev, lat->N);
+    OVL_LAUNCH_CHECK(lat);
+    return OVL_OK;
+}
+
+int ovl_gemv_df(ovl_lattice lat, GemvDev* gd_dev, int nsolve, int maxcol, cudaStream_t st) {
+    (void)maxcol;
+    size_t blocks = (lat->N + 255) / 256;
+    size_t g = (size_t)lat->num_sms * 4;
+    if (blocks < g) g = blocks;
+    dim3 grid((unsigned)g, nsolve);
+    k_gemv<<<grid, 256, 0, st>>>(gd_dev, lat->N);
+    OVL_LAUNCH_CHECK(lat);
+    return OVL_OK;
+}
+
+int ovl_start_vector(ovl_lattice lat, const BatchDev& b, const double* beta2_dev, int beta_stride, cudaStream_t st) {
+    size_t blocks = (b.N + 255) / 256;
+    size_t g = (size_t)lat->num_sms * 4;
+    if (blocks < g) g = blocks;
+    dim3 grid((unsigned)g, b.nsolve);
+    if (b.df)
+        k_start<true><<<grid, 256, 0, st>>>(b, beta2_dev, beta_stride);
+    else
+        k_start<false><<<grid, 256, 0, st>>>(b, beta2_dev, beta_stride);
+    OVL_LAUNCH_CHECK(lat);
+    return OVL_OK;
+}

@@ -1,0 +1,84 @@
+// Batched Arnoldi machinery (Sec. 2, Eq. 7; Sec. 3, Eq. 14): device-side
+// descriptors shared by krylov.cu, newton.cu and sign.cu.
+#pragma once
+#include "ovl_common.cuh"
+
+#define OVL_MAXCOL 960  // m + k + 1 (columns of the augmented basis) per solve
+
+// One solve of a batch. All pointers are device memory.
+//
+// Q = (S_m  v_1 ... v_k) is the augmented basis of Eq. 14 (m = m_q; m_q = 0
+// for LR deflation and for no deflation). Column c lives at qhi[c] (FP32
+// high part, packed order) and, in the FP64 mode, qlo[c] (FP32 low part);
+// the two sum to a 48-bit value. H is the (m+k+1) x (m+k+1) matrix of
+// Eq. 15 (column-major, leading dimension ldH): H[0:m,0:m] = T_m,
+// H[0:m, m:] = S^dag A V (the X of Eq. 18), H[m:, m:] = H_k, plus the
+// sub-diagonal Arnoldi residual norms. H32 is an FP32 shadow of H.
+struct SolveDev {
+    const float2* const* qhi;
+    const float2* const* qlo;  // null in the mixed modes
+    double2* u;      // Arnoldi candidate (once orthogonalised, unnormalised)
+    double2* w;      // A u
+    double2* H;
+    float2* H32;
+    double2* dots;   // pass-A results: a[0..p), b[p..2p), g_uu, g_uw, g_ww
+    double2* dvec;   // d = H a  (p+1)
+    float2* ap;      // pass-B coefficients a/nu            (FP32)
+    float2* gh;      // pass-B coefficients g, high part    (FP32)
+    float2* gl;      // pass-B coefficients g, low part     (FP32)
+    double* scal;    // [0] 1/nu, [1..2] -e_p/nu (complex), [3] nu, [4] beta_k
+    int m_q;         // leading fixed columns (Schur vectors)
+    int k;           // requested Krylov depth
+    int ldH;
+    int active;      // cleared on breakdown or error
+    int k_used;
+    int status;      // OVL_* per solve
+};
+
+struct BatchDev {
+    SolveDev* sd;    // device array of nsolve descriptors
+    int nsolve;
+    size_t N;
+    double2* part;   // partial sums: nsolve x G x pstride
+    int G;           // CTAs per solve of the streaming passes
+    int pstride;     // >= 2*OVL_MAXCOL + 3
+    int* counters;   // nsolve ints (last-block detection), zero between launches
+    int pmax;        // max over solves of the basis columns used at this step
+    int df;          // FP64 mode: basis has low planes
+};
+
+// launchers (krylov.cu)
+int ovl_gs_dot(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st);
+int ovl_gs_reduce(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st);
+int ovl_gs_small(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st);
+int ovl_gs_update(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st);
+int ovl_gs_final(ovl_lattice lat, const BatchDev& b, cudaStream_t st);
+int ovl_gs_grid(ovl_lattice lat);
+
+// Accurate (FP64) projections used once per solve for the deflation step and
+// for the start vector: P[s][c] = sum_r conj(Q_s[r,c]) x_s[r] for c < ncol_s,
+// plus P[s][ncol_s] = |x_s|^2.
+struct ProjDev {
+    const float2* const* qhi;  // column pointers (ncol entries)
+    const float2* const* qlo;
+    double2* x;                // packed FP64 vector
+    double2* out;              // ncol + 1 results
+    const double2* coef;       // for the update: x -= sum_c Q[:,c] coef[c]
+    int ncol;
+};
+int ovl_proj_dot(ovl_lattice lat, ProjDev* pd_dev, int nsolve, int maxcol, double2* part, int G, cudaStream_t st);
+int ovl_proj_update(ovl_lattice lat, ProjDev* pd_dev, int nsolve, int maxcol, cudaStream_t st);
+
+// y_s = sum_c Q_s[:,c] g_s[c] (df accumulation), FP64 packed output.
+struct GemvDev {
+    const float2* const* qhi;
+    const float2* const* qlo;
+    const double2* g;
+    double2* y;
+    int ncol;
+};
+int ovl_gemv_df(ovl_lattice lat, GemvDev* gd_dev, int nsolve, int maxcol, cudaStream_t st);
+
+// v_1 = x / beta into column m_q of Q (split hi/lo) and into u.
+int ovl_start_vector(ovl_lattice lat, const BatchDev& b, const double* beta2_dev, int beta_stride,
+                     cudaStream_t st);

@@ -1,0 +1,310 @@
+// Sign of the small projected matrix by the scaled Newton (Roberts)
+// iteration (the matrix iterations Sec. 2 refers to; used for f(H_k) in
+// Eqs. 11 and 22 and for f(H) on the whole block matrix of Eqs. 15-17):
+//   X_0 = H,  X_{i+1} = (c_i X_i + X_i^{-1} / c_i) / 2,  c_i = |det X_i|^{-1/n},
+// scaling dropped once |X_{i+1} - X_i|_F < 1e-2 |X_{i+1}|_F, stopped at
+// |X_{i+1} - X_i|_F <= tol |X_{i+1}|_F.
+//
+// One cooperative launch runs every iteration of every solve of a batch. The
+// CTAs of one solve form a group that owns the matrix rows round-robin and
+// inverts X_i by Gauss-Jordan elimination with partial pivoting (pivot rows
+// chosen implicitly, no row swaps); the group meets at one barrier per pivot.
+// Barriers are counters in global memory with a bounded wait: a wait that
+// runs out sets OVL_ETIMEOUT for the solve and every CTA of the group leaves.
+#include "newton.cuh"
+
+namespace {
+
+constexpr int NT = 256;
+constexpr long long SPIN_LIMIT = 1ll << 24;  // polls of ~100 ns: about 2 s
+
+struct Group {
+    NewtonDev* nd;
+    int s, g, cpm;
+};
+
+// Barrier for the CTAs of one solve. Returns false if it timed out here or
+// anywhere else in the group.
+__device__ bool group_sync(NewtonDev& d, unsigned& gen, int cpm) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        gen++;
+        unsigned target = gen * (unsigned)cpm;
+        __threadfence();
+        atomicAdd(d.bar, 1u);
+        long long it = 0;
+        int good = 1;
+        while (true) {
+            unsigned v = *((volatile unsigned*)d.bar);
+            if (v >= target) break;
+            if (*((volatile int*)d.status) == OVL_ETIMEOUT) {
+                good = 0;
+                break;
+            }
+            if (++it > SPIN_LIMIT) {
+                atomicExch(d.status, OVL_ETIMEOUT);
+                good = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__device__ __forceinline__ double warp_maxloc(double v, int& idx) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ov > v || (ov == v && oi < idx)) {
+            v = ov;
+            idx = oi;
+        }
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(NT) k_newton(NewtonDev* nds, int nsolve, int cpm) {
+    const int s = blockIdx.x / cpm;
+    const int g = blockIdx.x % cpm;
+    if (s >= nsolve) return;
+    NewtonDev& d = nds[s];
+    if (!d.run) return;
+    const int n = d.n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double2* __restrict__ X = d.X;
+    double2* __restrict__ W = d.W;
+    __shared__ double2 prow[2][OVL_NEWTON_MAXN];
+    __shared__ unsigned char used[OVL_NEWTON_MAXN];
+    __shared__ int piv[OVL_NEWTON_MAXN];
+    __shared__ double s_red[NT / 32][2];
+    __shared__ int s_idx[NT / 32];
+    unsigned gen = 0;
+    // X_0 = H (column-major input, row-major iterate)
+    for (int i = g; i < n; i += cpm)
+        for (int l = tid; l < n; l += NT) X[(size_t)i * n + l] = d.H[i + (size_t)l * d.ldH];
+    bool scaling = true;
+    int iter = 0;
+    bool converged = false;
+    if (!group_sync(d, gen, cpm)) return;
+    while (iter < d.max_iter) {
+        iter++;
+        // W = X for own rows, candidates for column 0
+        for (int i = tid; i < n; i += NT) used[i] = 0;
+        for (int i = g; i < n; i += cpm)
+            for (int l = tid; l < n; l += NT) W[(size_t)i * n + l] = X[(size_t)i * n + l];
+        __syncthreads();
+        double logdet = 0.0;
+        int bad = 0;
+        for (int k = 0; k < n; k++) {
+            // candidate of this CTA for column k among unused own rows
+            {
+                double best = -1.0;
+                int bi = 0x7fffffff;
+                for (int i = g + cpm * tid; i < n; i += cpm * NT)
+                    if (!used[i]) {
+                        double v = cabs2(W[(size_t)i * n + k]);
+                        if (v > best || (v == best && i < bi)) {
+                            best = v;
+                            bi = i;
+                        }
+                    }
+                best = warp_maxloc(best, bi);
+                if (lane == 0) {
+                    s_red[warp][0] = best;
+                    s_idx[warp] = bi;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    for (int w = 1; w < NT / 32; w++)
+                        if (s_red[w][0] > best || (s_red[w][0] == best && s_idx[w] < bi)) {
+                            best = s_red[w][0];
+                            bi = s_idx[w];
+                        }
+                    // two buffers by step parity: a CTA one step ahead cannot
+                    // overwrite what a slower one is still reading
+                    d.cand_val[(k & 1) * cpm + g] = best;
+                    d.cand_row[(k & 1) * cpm + g] = bi;
+                }
+            }
+            if (!group_sync(d, gen, cpm)) return;
+            // global pivot (identical choice in every CTA)
+            double best = -1.0;
+            int pr = 0x7fffffff;
+            for (int q = 0; q < cpm; q++) {
+                double v = ((volatile double*)d.cand_val)[(k & 1) * cpm + q];
+                int r = ((volatile int*)d.cand_row)[(k & 1) * cpm + q];
+                if (v > best || (v == best && r < pr)) {
+                    best = v;
+                    pr = r;
+                }
+            }
+            if (!(best > 0.0) || pr < 0 || pr >= n) {
+                bad = 1;
+                break;
+            }
+            const int buf = k & 1;
+            // deferred write-back of the previous pivot row (its owner only)
+            if (k > 0) {
+                int pp = piv[k - 1];
+                if (pp % cpm == g)
+                    for (int l = tid; l < n; l += NT) W[(size_t)pp * n + l] = prow[buf ^ 1][l];
+            }
+            double2 pv = W[(size_t)pr * n + k];
+            double2 inv = cinv(pv);
+            for (int l = tid; l < n; l += NT) {
+                double2 v = W[(size_t)pr * n + l];
+                prow[buf][l] = (l == k) ? inv : cmul(v, inv);
+            }
+            if (tid == 0) {
+                used[pr] = 1;
+                piv[k] = pr;
+            }
+            logdet += 0.5 * log(cabs2(pv));
+            __syncthreads();
+            // eliminate own rows i != pr
+            for (int i = g + cpm * warp; i < n; i += cpm * (NT / 32)) {
+                if (i == pr) continue;
+                double2* row = W + (size_t)i * n;
+                double2 f = row[k];
+                __syncwarp();
+                for (int l = lane; l < n; l += 32) {
+                    double2 pl = prow[buf][l];
+                    if (l == k) {
+                        row[l] = make_double2(-(f.x * pl.x - f.y * pl.y), -(f.x * pl.y + f.y * pl.x));
+                    } else {
+                        double2 v = row[l];
+                        v.x -= f.x * pl.x - f.y * pl.y;
+                        v.y -= f.x * pl.y + f.y * pl.x;
+                        row[l] = v;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (bad) {
+            if (tid == 0 && g == 0) atomicExch(d.status, OVL_ENOCONV);
+            return;
+        }
+        // last pivot row write-back, then every row of the inverse is final
+        {
+            int pp = piv[n - 1];
+            if (pp % cpm == g)
+                for (int l = tid; l < n; l += NT) W[(size_t)pp * n + l] = prow[(n - 1) & 1][l];
+        }
+        if (!group_sync(d, gen, cpm)) return;
+        // X_new[i][piv_j] = (c X[i][piv_j] + W[piv_i][j] / c) / 2
+        const double c = scaling ? exp(-logdet / n) : 1.0;
+        const double ic = 1.0 / c;
+        double dsum = 0.0, nsum = 0.0;
+        for (int i = g + cpm * warp; i < n; i += cpm * (NT / 32)) {
+            const double2* st = W + (size_t)piv[i] * n;
+            double2* xr = X + (size_t)i * n;
+            for (int j = lane; j < n; j += 32) {
+                int l = piv[j];
+                double2 xo = xr[l];
+                double2 a = st[j];
+                double2 xn = make_double2(0.5 * (c * xo.x + ic * a.x), 0.5 * (c * xo.y + ic * a.y));
+                dsum += cabs2(csub(xn, xo));
+                nsum += cabs2(xn);
+                xr[l] = xn;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+            nsum += __shfl_xor_sync(0xffffffffu, nsum, o);
+        }
+        if (lane == 0) {
+            s_red[warp][0] = dsum;
+            s_red[warp][1] = nsum;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0.0, b = 0.0;
+            for (int w = 0; w < NT / 32; w++) {
+                a += s_red[w][0];
+                b += s_red[w][1];
+            }
+            d.red[2 * g] = a;
+            d.red[2 * g + 1] = b;
+        }
+        if (!group_sync(d, gen, cpm)) return;
+        double D = 0.0, Nn = 0.0;
+        for (int q = 0; q < cpm; q++) {
+            D += ((volatile double*)d.red)[2 * q];
+            Nn += ((volatile double*)d.red)[2 * q + 1];
+        }
+        const double diff = sqrt(D), nrm = sqrt(Nn);
+        if (diff < 1e-2 * nrm) scaling = false;
+        if (diff <= d.tol * nrm) {
+            converged = true;
+            break;
+        }
+        if (!(nrm == nrm)) break;
+    }
+    if (g == 0 && tid == 0) {
+        *d.iters = iter;
+        if (!converged) atomicCAS(d.status, 0, OVL_ENOCONV);
+    }
+}
+
+// y_s = F_s c_s for the coefficient vectors (F row-major n x n)
+__global__ void __launch_bounds__(256) k_fmatvec(NewtonDev* nds, int nsolve) {
+    const int s = blockIdx.y;
+    NewtonDev& d = nds[s];
+    if (!d.run) return;
+    const int n = d.n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 8 + warp;
+    if (i >= n) return;
+    const double2* row = d.X + (size_t)i * n;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int l = lane; l < n; l += 32) {
+        double2 a = row[l], b = d.cvec[l];
+        acc.x += a.x * b.x - a.y * b.y;
+        acc.y += a.x * b.y + a.y * b.x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) d.gout[i] = acc;
+}
+
+}  // namespace
+
+int ovl_newton_cpm(ovl_lattice lat, int nsolve, int nmax) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_newton, NT, 0);
+    if (per_sm < 1) per_sm = 1;
+    int cap = lat->num_sms * per_sm;
+    int cpm = cap / (nsolve > 0 ? nsolve : 1);
+    int want = (nmax + 7) / 8;  // at least 8 rows per CTA
+    if (cpm > want) cpm = want;
+    if (cpm > 64) cpm = 64;
+    if (cpm < 1) cpm = 1;
+    return cpm;
+}
+
+int ovl_newton_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int cpm, cudaStream_t st) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_newton, NT, 0);
+    if ((long)nsolve * cpm > (long)lat->num_sms * per_sm)
+        return ovl_fail(lat, OVL_EINVAL, "Newton batch of %d x %d blocks exceeds co-residency (%d)", nsolve, cpm,
+                        lat->num_sms * per_sm);
+    void* args[] = {(void*)&nd_dev, (void*)&nsolve, (void*)&cpm};
+    OVL_CUDA_TRY(lat, cudaLaunchCooperativeKernel((const void*)k_newton, dim3(nsolve * cpm), dim3(NT), args, 0, st));
+    return OVL_OK;
+}
+
+int ovl_fmatvec_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int nmax, cudaStream_t st) {
+    dim3 grid((nmax + 7) / 8, nsolve);
+    k_fmatvec<<<grid, 256, 0, st>>>(nd_dev, nsolve);
+    OVL_LAUNCH_CHECK(lat);
+    return OVL_OK;
+}

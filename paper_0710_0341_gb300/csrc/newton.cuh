@@ -1,0 +1,28 @@
+// Scaled Newton iteration for the sign of the small projected matrix.
+#pragma once
+#include "ovl_common.cuh"
+
+#define OVL_NEWTON_MAXN 960
+
+struct NewtonDev {
+    const double2* H;  // input, column-major, leading dimension ldH
+    int ldH;
+    int n;             // matrix order (0 < n <= OVL_NEWTON_MAXN)
+    int run;           // 0: skip this solve
+    int max_iter;
+    double tol;
+    double2* X;        // n x n row-major: iterate, and sgn(H) on exit
+    double2* W;        // n x n row-major work (inverse in place)
+    double* cand_val;  // 2 x CTAs of the group (step parity)
+    int* cand_row;
+    double* red;       // 2 per CTA of the group
+    unsigned* bar;     // group barrier counter (zero before launch)
+    int* status;       // OVL_* (zero before launch)
+    int* iters;
+    const double2* cvec;  // coefficient vector (n) for F c
+    double2* gout;        // F c (n)
+};
+
+int ovl_newton_cpm(ovl_lattice lat, int nsolve, int nmax);
+int ovl_newton_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int cpm, cudaStream_t st);
+int ovl_fmatvec_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int nmax, cudaStream_t st);

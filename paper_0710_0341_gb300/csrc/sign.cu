@@ -1,0 +1,666 @@
+// Deflation data and the batched sign-function driver (Secs. 2-4).
+//
+// ovl_sign_apply runs, for every solve of a batch, on the device:
+//   deflation projection  Schur: x_perp = (1 - S S^dag) b (twice)      (Sec. 3)
+//                         LR:    g = L^dag b, x_minus = b - R g        (Eq. 21)
+//   start vector          beta = |x|, v_1 = x / beta                   (Eq. 7)
+//   k Arnoldi steps       stencil + two Gram-Schmidt passes per step   (Eqs. 7, 14)
+//   small sign            F = sgn(H) by scaled Newton                  (Eqs. 11, 16-17, 22)
+//   recombination         Schur: y = (S V_k) F (S^dag b; beta e_1)     (Eq. 16 = Eq. 19)
+//                         LR:    y = R sgn(Lambda) g + beta V_k F e_1  (Eq. 22)
+// The host only sizes buffers, launches kernels and reads back three small
+// arrays (the projection coefficients, the solve descriptors and the
+// Newton status); every arithmetic step runs in the kernels of this library.
+#include <math.h>
+
+#include <algorithm>
+
+#include "df.cuh"
+#include "krylov.cuh"
+#include "newton.cuh"
+
+namespace {
+
+__global__ void k_split_planes(const double2* __restrict__ x, float2* __restrict__ hi, float2* __restrict__ lo,
+                               size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double2 v = x[i];
+        float2 a = split_d(v.x), b = split_d(v.y);
+        hi[i] = make_float2(a.x, b.x);
+        lo[i] = make_float2(a.y, b.y);
+    }
+}
+
+__global__ void k_join_planes(const float2* __restrict__ hi, const float2* __restrict__ lo, double2* __restrict__ x,
+                              size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float2 a = hi[i], b = lo[i];
+        x[i] = make_double2((double)a.x + (double)b.x, (double)a.y + (double)b.y);
+    }
+}
+
+__global__ void k_h_to_h32(const double2* __restrict__ H, float2* __restrict__ H32, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        H32[i] = make_float2((float)H[i].x, (float)H[i].y);
+}
+
+struct Carve {
+    char* base;
+    size_t off = 0;
+    template <class T>
+    T* take(size_t n) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = (T*)(base + off);
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+unsigned grid_for(size_t n, int sms) {
+    size_t b = (n + 255) / 256;
+    size_t cap = (size_t)sms * 8;
+    return (unsigned)std::max<size_t>(1, std::min(b, cap));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// deflation data
+// ---------------------------------------------------------------------------
+static int upload_vectors(ovl_lattice lat, const double* canon, int m, float2** hi, float2** lo) {
+    size_t N = lat->N;
+    size_t vb = N * sizeof(double2) * (size_t)m;
+    if (cudaMalloc(hi, N * sizeof(float2) * m) != cudaSuccess || cudaMalloc(lo, N * sizeof(float2) * m) != cudaSuccess) {
+        cudaGetLastError();
+        return ovl_fail(lat, OVL_ENOMEM, "deflation vectors: allocation failed");
+    }
+    // canonical (host or device) -> packed FP64 (scratch) -> hi/lo planes
+    void* s;
+    if (int rc = ovl_scratch(lat, 2 * vb, &s)) return rc;
+    const double* src = canon;
+    if (!ovl_is_device_ptr(canon)) {
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(s, canon, vb, cudaMemcpyHostToDevice, lat->stream));
+        src = (const double*)s;
+    }
+    double2* packed = (double2*)((char*)s + vb);
+    if (int rc = ovl_pack_impl(lat, src, packed, m, OVL_VEC_F64, lat->stream)) return rc;
+    k_split_planes<<<grid_for(N * m, lat->num_sms), 256, 0, lat->stream>>>(packed, *hi, *lo, N * m);
+    OVL_LAUNCH_CHECK(lat);
+    OVL_CUDA_TRY(lat, cudaStreamSynchronize(lat->stream));
+    return OVL_OK;
+}
+
+extern "C" int ovl_destroy_deflation(ovl_deflation d) {
+    if (!d) return OVL_OK;
+    if (d->lat) cudaStreamSynchronize(d->lat->stream);
+    cudaFree(d->S_hi);
+    cudaFree(d->S_lo);
+    cudaFree(d->L_hi);
+    cudaFree(d->L_lo);
+    cudaFree(d->T);
+    delete d;
+    return OVL_OK;
+}
+
+extern "C" int ovl_set_deflation(ovl_lattice lat, double mu, double m_w, int scheme, int m, const double* S_or_R,
+                                 const double* T, const double* L, ovl_deflation* out) {
+    if (!lat || !out || !S_or_R || !T) return ovl_fail(lat, OVL_EINVAL, "ovl_set_deflation: null argument");
+    if (scheme != OVL_DEFL_SCHUR && scheme != OVL_DEFL_LR)
+        return ovl_fail(lat, OVL_EINVAL, "ovl_set_deflation: scheme %d is not Schur or LR", scheme);
+    if (m < 1 || (size_t)m >= lat->N || m > 256) return ovl_fail(lat, OVL_EINVAL, "ovl_set_deflation: m=%d", m);
+    if (scheme == OVL_DEFL_LR && !L) return ovl_fail(lat, OVL_EINVAL, "ovl_set_deflation: LR needs L");
+    if (scheme == OVL_DEFL_SCHUR && L) return ovl_fail(lat, OVL_EINVAL, "ovl_set_deflation: Schur takes no L");
+    ovl_deflation d = new ovl_deflation_s();
+    d->lat = lat;
+    d->scheme = scheme;
+    d->m = m;
+    d->mu = mu;
+    d->m_w = m_w;
+    int rc = upload_vectors(lat, S_or_R, m, &d->S_hi, &d->S_lo);
+    if (!rc && scheme == OVL_DEFL_LR) rc = upload_vectors(lat, L, m, &d->L_hi, &d->L_lo);
+    if (rc) {
+        ovl_destroy_deflation(d);
+        return rc;
+    }
+    size_t tn = scheme == OVL_DEFL_SCHUR ? (size_t)m * m : (size_t)m;
+    d->T_host.resize(2 * tn);
+    if (ovl_is_device_ptr(T)) {
+        if (cudaMemcpy(d->T_host.data(), T, tn * sizeof(double2), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            ovl_destroy_deflation(d);
+            return ovl_fail(lat, OVL_ECUDA, "ovl_set_deflation: copying T failed");
+        }
+    } else {
+        memcpy(d->T_host.data(), T, tn * sizeof(double2));
+    }
+    for (double v : d->T_host)
+        if (!(v == v)) {
+            ovl_destroy_deflation(d);
+            return ovl_fail(lat, OVL_EINVAL, "ovl_set_deflation: T/Lambda has NaN");
+        }
+    if (cudaMalloc(&d->T, tn * sizeof(double2)) != cudaSuccess ||
+        cudaMemcpy(d->T, d->T_host.data(), tn * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        ovl_destroy_deflation(d);
+        return ovl_fail(lat, OVL_ENOMEM, "ovl_set_deflation: T allocation failed");
+    }
+    *out = d;
+    return OVL_OK;
+}
+
+static int download_vectors(ovl_lattice lat, const float2* hi, const float2* lo, int m, double* canon) {
+    size_t N = lat->N;
+    size_t vb = N * sizeof(double2) * (size_t)m;
+    void* s;
+    if (int rc = ovl_scratch(lat, 2 * vb, &s)) return rc;
+    double2* packed = (double2*)s;
+    double2* cdev = (double2*)((char*)s + vb);
+    k_join_planes<<<grid_for(N * m, lat->num_sms), 256, 0, lat->stream>>>(hi, lo, packed, N * m);
+    OVL_LAUNCH_CHECK(lat);
+    bool dev = ovl_is_device_ptr(canon);
+    if (int rc = ovl_unpack_impl(lat, packed, dev ? canon : (double*)cdev, m, OVL_VEC_F64, lat->stream)) return rc;
+    if (!dev) OVL_CUDA_TRY(lat, cudaMemcpyAsync(canon, cdev, vb, cudaMemcpyDeviceToHost, lat->stream));
+    OVL_CUDA_TRY(lat, cudaStreamSynchronize(lat->stream));
+    return OVL_OK;
+}
+
+extern "C" int ovl_get_deflation(ovl_deflation d, int* scheme, int* m, double* S_or_R, double* T, double* L) {
+    if (!d) return ovl_fail(nullptr, OVL_EINVAL, "ovl_get_deflation: null handle");
+    ovl_lattice lat = d->lat;
+    if (scheme) *scheme = d->scheme;
+    if (m) *m = d->m;
+    if (S_or_R)
+        if (int rc = download_vectors(lat, d->S_hi, d->S_lo, d->m, S_or_R)) return rc;
+    if (L && d->scheme == OVL_DEFL_LR)
+        if (int rc = download_vectors(lat, d->L_hi, d->L_lo, d->m, L)) return rc;
+    if (T) {
+        size_t tb = d->T_host.size() * sizeof(double);
+        if (ovl_is_device_ptr(T))
+            OVL_CUDA_TRY(lat, cudaMemcpy(T, d->T_host.data(), tb, cudaMemcpyHostToDevice));
+        else
+            memcpy(T, d->T_host.data(), tb);
+    }
+    return OVL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the sign function
+// ---------------------------------------------------------------------------
+namespace {
+
+struct SolvePlan {
+    int m_q = 0, m_defl = 0, scheme = OVL_DEFL_NONE, k = 0, ldH = 0, nmax = 0;
+    ovl_deflation d = nullptr;
+    // device pieces
+    float2 *Vhi = nullptr, *Vlo = nullptr;
+    double2 *u = nullptr, *w = nullptr, *H = nullptr;
+    float2* H32 = nullptr;
+    double2 *dots = nullptr, *dvec = nullptr;
+    float2 *ap = nullptr, *gh = nullptr, *gl = nullptr;
+    double* scal = nullptr;
+    const float2** qhi = nullptr;
+    const float2** qlo = nullptr;
+    double2 *X = nullptr, *W = nullptr;
+    double *cand_val = nullptr, *red = nullptr;
+    int* cand_row = nullptr;
+    unsigned* bar = nullptr;
+    int *nstat = nullptr, *iters = nullptr;
+    double2 *cvec = nullptr, *gcomb = nullptr;
+    double2 *pout1 = nullptr, *pout2 = nullptr, *pout3 = nullptr;
+    const float2 **pc_hi = nullptr, **pc_lo = nullptr;   // projection columns (dot)
+    const float2 **pu_hi = nullptr, **pu_lo = nullptr;   // projection columns (update)
+    const float2 **gc_hi = nullptr, **gc_lo = nullptr;   // recombination columns
+};
+
+}  // namespace
+
+extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params* params, const ovl_deflation* defl,
+                              const double* b, double* y, ovl_sign_info* info) {
+    if (!lat || nsolve < 1 || !params || !b || !y) return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: bad argument");
+    if (!lat->have_links) return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: links not set");
+    if (nsolve > 4096) return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: nsolve=%d too large", nsolve);
+    const size_t N = lat->N;
+    const int prec = params[0].prec;
+    const double m_w = params[0].m_w;
+    if (prec < OVL_PREC_FP64 || prec > OVL_PREC_MIXED_R12)
+        return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: precision %d unknown", prec);
+    const bool df = prec == OVL_PREC_FP64;
+    std::vector<SolvePlan> P(nsolve);
+    int kmax = 0, ldmax = 0, mdef_max = 0;
+    for (int i = 0; i < nsolve; i++) {
+        const ovl_sign_params& q = params[i];
+        if (q.prec != prec) return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: mixed precisions in one batch");
+        if (q.m_w != m_w) return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: one m_w per batch");
+        if (!(q.m_w > -4.0 + 1e-12) || !(q.mu == q.mu) || fabs(q.mu) > 50.0)
+            return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: solve %d: bad mu/m_w", i);
+        if (q.k < 1) return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: solve %d: k=%d < 1", i, q.k);
+        SolvePlan& p = P[i];
+        p.k = q.k;
+        if (defl && defl[i]) {
+            ovl_deflation d = defl[i];
+            if (d->lat != lat) return ovl_fail(lat, OVL_EINVAL, "solve %d: deflation of another lattice", i);
+            if (fabs(d->mu - q.mu) > 1e-12 || fabs(d->m_w - q.m_w) > 1e-12)
+                return ovl_fail(lat, OVL_EINVAL, "solve %d: deflation built for mu=%g m_w=%g, solve has mu=%g m_w=%g", i,
+                                d->mu, d->m_w, q.mu, q.m_w);
+            p.d = d;
+            p.scheme = d->scheme;
+            p.m_defl = d->m;
+            p.m_q = d->scheme == OVL_DEFL_SCHUR ? d->m : 0;
+        }
+        p.ldH = p.m_q + p.k + 1;
+        p.nmax = p.m_q + p.k;
+        if (p.ldH > OVL_MAXCOL || p.nmax > OVL_NEWTON_MAXN)
+            return ovl_fail(lat, OVL_EINVAL, "solve %d: m+k+1=%d exceeds the build limit %d", i, p.ldH, OVL_MAXCOL);
+        if ((size_t)p.k + 1 > N) return ovl_fail(lat, OVL_EINVAL, "solve %d: k=%d exceeds N", i, p.k);
+        kmax = std::max(kmax, p.k);
+        ldmax = std::max(ldmax, p.ldH);
+        mdef_max = std::max(mdef_max, p.m_defl);
+    }
+    const int G = ovl_gs_grid(lat);
+    const int pstride = std::max(2 * ldmax + 3, mdef_max + 1);
+    const int cpm = ovl_newton_cpm(lat, nsolve, ldmax);
+    // ---- sizes and one allocation ----
+    auto plan_bytes = [&](bool carve, char* base) -> size_t {
+        Carve c{base};
+        for (int i = 0; i < nsolve; i++) {
+            SolvePlan& p = P[i];
+            size_t ld = p.ldH, nm = p.nmax, md = std::max(1, p.m_defl);
+            auto t = [&](auto*& ptr, size_t n) {
+                using T = std::remove_reference_t<decltype(*ptr)>;
+                T* q = c.take<std::remove_const_t<T>>(n);
+                if (carve) ptr = q;
+            };
+            t(p.Vhi, N * (p.k + 1));
+            if (df) t(p.Vlo, N * (p.k + 1));
+            t(p.u, N);
+            t(p.w, N);
+            t(p.H, ld * ld);
+            t(p.H32, ld * ld);
+            t(p.dots, 2 * ld + 3);
+            t(p.dvec, ld + 1);
+            t(p.ap, ld);
+            t(p.gh, ld);
+            t(p.gl, ld);
+            t(p.scal, 8);
+            t(p.qhi, ld);
+            t(p.qlo, ld);
+            t(p.X, nm * nm);
+            t(p.W, nm * nm);
+            t(p.cand_val, 128);
+            t(p.cand_row, 128);
+            t(p.red, 128);
+            t(p.bar, 1);
+            t(p.nstat, 1);
+            t(p.iters, 1);
+            t(p.cvec, nm + md);
+            t(p.gcomb, nm + md);
+            t(p.pout1, md + 1);
+            t(p.pout2, md + 1);
+            t(p.pout3, md + 1);
+            t(p.pc_hi, md);
+            t(p.pc_lo, md);
+            t(p.pu_hi, md);
+            t(p.pu_lo, md);
+            t(p.gc_hi, nm + md);
+            t(p.gc_lo, nm + md);
+        }
+        c.take<char>(0);
+        return c.off;
+    };
+    size_t per = plan_bytes(false, nullptr);
+    size_t batch_off;
+    {
+        Carve c{nullptr};
+        c.off = per;
+        c.take<SolveDev>(nsolve);
+        c.take<NewtonDev>(nsolve);
+        c.take<ProjDev>(nsolve);
+        c.take<GemvDev>(nsolve);
+        c.take<double2>((size_t)nsolve * G * pstride);
+        c.take<int>(nsolve);
+        c.take<double>(nsolve);
+        c.take<void*>(2 * (size_t)nsolve);
+        c.take<double2>(N * nsolve);  // canonical staging for host b / y
+        c.take<char>(0);
+        batch_off = c.off;
+    }
+    if (batch_off > lat->ws_bytes) {
+        cudaStreamSynchronize(lat->stream);
+        cudaFree(lat->ws);
+        lat->ws = nullptr;
+        lat->ws_bytes = 0;
+        if (cudaMalloc(&lat->ws, batch_off) != cudaSuccess) {
+            cudaGetLastError();
+            return ovl_fail(lat, OVL_ENOMEM, "ovl_sign_apply: workspace of %.3f GB does not fit", batch_off / 1e9);
+        }
+        lat->ws_bytes = batch_off;
+    }
+    char* base = (char*)lat->ws;
+    plan_bytes(true, base);
+    Carve c{base};
+    c.off = per;
+    SolveDev* d_sd = c.take<SolveDev>(nsolve);
+    NewtonDev* d_nd = c.take<NewtonDev>(nsolve);
+    ProjDev* d_pd = c.take<ProjDev>(nsolve);
+    GemvDev* d_gd = c.take<GemvDev>(nsolve);
+    double2* d_part = c.take<double2>((size_t)nsolve * G * pstride);
+    int* d_counters = c.take<int>(nsolve);
+    double* d_mu = c.take<double>(nsolve);
+    void** d_ptrs = c.take<void*>(2 * (size_t)nsolve);
+    double2* d_canon = c.take<double2>(N * nsolve);
+    cudaStream_t st = lat->stream;
+
+    // ---- inputs ----
+    const double* bsrc = b;
+    if (!ovl_is_device_ptr(b)) {
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_canon, b, N * sizeof(double2) * nsolve, cudaMemcpyHostToDevice, st));
+        bsrc = (const double*)d_canon;
+    }
+    for (int i = 0; i < nsolve; i++)
+        if (int rc = ovl_pack_impl(lat, bsrc + 2 * N * i, P[i].u, 1, OVL_VEC_F64, st)) return rc;
+    OVL_CUDA_TRY(lat, cudaMemsetAsync(d_counters, 0, nsolve * sizeof(int), st));
+
+    // ---- column pointers, descriptors ----
+    std::vector<SolveDev> hs(nsolve);
+    std::vector<const float2*> tmp_hi, tmp_lo;
+    for (int i = 0; i < nsolve; i++) {
+        SolvePlan& p = P[i];
+        tmp_hi.assign(p.ldH, nullptr);
+        tmp_lo.assign(p.ldH, nullptr);
+        for (int cidx = 0; cidx < p.m_q; cidx++) {
+            tmp_hi[cidx] = p.d->S_hi + N * cidx;
+            tmp_lo[cidx] = p.d->S_lo + N * cidx;
+        }
+        for (int cidx = p.m_q; cidx < p.ldH; cidx++) {
+            tmp_hi[cidx] = p.Vhi + N * (cidx - p.m_q);
+            tmp_lo[cidx] = df ? p.Vlo + N * (cidx - p.m_q) : nullptr;
+        }
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(p.qhi, tmp_hi.data(), p.ldH * sizeof(void*), cudaMemcpyHostToDevice, st));
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(p.qlo, tmp_lo.data(), p.ldH * sizeof(void*), cudaMemcpyHostToDevice, st));
+        OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));  // tmp vectors are reused
+        SolveDev& s = hs[i];
+        s.qhi = p.qhi;
+        s.qlo = df ? p.qlo : nullptr;
+        s.u = p.u;
+        s.w = p.w;
+        s.H = p.H;
+        s.H32 = p.H32;
+        s.dots = p.dots;
+        s.dvec = p.dvec;
+        s.ap = p.ap;
+        s.gh = p.gh;
+        s.gl = p.gl;
+        s.scal = p.scal;
+        s.m_q = p.m_q;
+        s.k = p.k;
+        s.ldH = p.ldH;
+        s.active = 1;
+        s.k_used = p.k;
+        s.status = 0;
+        OVL_CUDA_TRY(lat, cudaMemsetAsync(p.H, 0, (size_t)p.ldH * p.ldH * sizeof(double2), st));
+        if (p.m_q)
+            OVL_CUDA_TRY(lat, cudaMemcpy2DAsync(p.H, p.ldH * sizeof(double2), p.d->T, p.m_q * sizeof(double2),
+                                                p.m_q * sizeof(double2), p.m_q, cudaMemcpyDeviceToDevice, st));
+        k_h_to_h32<<<grid_for((size_t)p.ldH * p.ldH, lat->num_sms), 256, 0, st>>>(p.H, p.H32,
+                                                                                  (size_t)p.ldH * p.ldH);
+        OVL_LAUNCH_CHECK(lat);
+    }
+    OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_sd, hs.data(), nsolve * sizeof(SolveDev), cudaMemcpyHostToDevice, st));
+
+    // ---- deflation projection and |x|^2 ----
+    auto run_proj = [&](int which) -> int {
+        // which 0: first dot (S or L), 1: second dot (Schur only), 2: norm only
+        std::vector<ProjDev> pd(nsolve);
+        int maxcol = 0;
+        for (int i = 0; i < nsolve; i++) {
+            SolvePlan& p = P[i];
+            ProjDev& q = pd[i];
+            q.x = p.u;
+            q.ncol = (which == 2 || p.scheme == OVL_DEFL_NONE || (which == 1 && p.scheme != OVL_DEFL_SCHUR)) ? 0 : p.m_defl;
+            q.out = which == 0 ? p.pout1 : which == 1 ? p.pout2 : p.pout3;
+            q.qhi = p.pc_hi;
+            q.qlo = p.pc_lo;
+            q.coef = q.out;
+            maxcol = std::max(maxcol, q.ncol);
+        }
+        if (int rc = cudaMemcpyAsync(d_pd, pd.data(), nsolve * sizeof(ProjDev), cudaMemcpyHostToDevice, st))
+            return ovl_fail(lat, OVL_ECUDA, "copy failed (%d)", rc);
+        if (int rc = ovl_proj_dot(lat, d_pd, nsolve, maxcol, d_part, G, st)) return rc;
+        if (which == 2 || maxcol == 0) return cudaStreamSynchronize(st) == cudaSuccess ? OVL_OK : OVL_ECUDA;
+        // update x -= Q coef with the update columns (S for Schur, R for LR)
+        for (int i = 0; i < nsolve; i++) {
+            pd[i].qhi = P[i].pu_hi;
+            pd[i].qlo = P[i].pu_lo;
+        }
+        if (int rc = cudaMemcpyAsync(d_pd, pd.data(), nsolve * sizeof(ProjDev), cudaMemcpyHostToDevice, st))
+            return ovl_fail(lat, OVL_ECUDA, "copy failed (%d)", rc);
+        if (int rc = ovl_proj_update(lat, d_pd, nsolve, maxcol, st)) return rc;
+        return cudaStreamSynchronize(st) == cudaSuccess ? OVL_OK : OVL_ECUDA;
+    };
+    for (int i = 0; i < nsolve; i++) {
+        SolvePlan& p = P[i];
+        if (!p.m_defl) continue;
+        std::vector<const float2*> dh(p.m_defl), dl(p.m_defl), uh(p.m_defl), ul(p.m_defl);
+        for (int cidx = 0; cidx < p.m_defl; cidx++) {
+            bool lr = p.scheme == OVL_DEFL_LR;
+            dh[cidx] = (lr ? p.d->L_hi : p.d->S_hi) + N * cidx;
+            dl[cidx] = (lr ? p.d->L_lo : p.d->S_lo) + N * cidx;
+            uh[cidx] = p.d->S_hi + N * cidx;
+            ul[cidx] = p.d->S_lo + N * cidx;
+        }
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(p.pc_hi, dh.data(), p.m_defl * sizeof(void*), cudaMemcpyHostToDevice, st));
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(p.pc_lo, dl.data(), p.m_defl * sizeof(void*), cudaMemcpyHostToDevice, st));
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(p.pu_hi, uh.data(), p.m_defl * sizeof(void*), cudaMemcpyHostToDevice, st));
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(p.pu_lo, ul.data(), p.m_defl * sizeof(void*), cudaMemcpyHostToDevice, st));
+        OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
+    }
+    if (int rc = run_proj(0)) return rc;
+    if (int rc = run_proj(1)) return rc;
+    if (int rc = run_proj(2)) return rc;
+    // projection coefficients back to the host (m + 1 numbers per solve)
+    std::vector<std::vector<double2>> c1(nsolve), c2(nsolve), nrm(nsolve);
+    std::vector<double> beta(nsolve);
+    for (int i = 0; i < nsolve; i++) {
+        SolvePlan& p = P[i];
+        int m = p.m_defl;
+        c1[i].resize(m + 1);
+        c2[i].resize(m + 1);
+        nrm[i].resize(1);
+        if (m) OVL_CUDA_TRY(lat, cudaMemcpy(c1[i].data(), p.pout1, m * sizeof(double2), cudaMemcpyDeviceToHost));
+        if (m && p.scheme == OVL_DEFL_SCHUR)
+            OVL_CUDA_TRY(lat, cudaMemcpy(c2[i].data(), p.pout2, m * sizeof(double2), cudaMemcpyDeviceToHost));
+        OVL_CUDA_TRY(lat, cudaMemcpy(nrm[i].data(), p.pout3, sizeof(double2), cudaMemcpyDeviceToHost));
+        beta[i] = sqrt(nrm[i][0].x);
+    }
+
+    // ---- start vectors ----
+    BatchDev bd;
+    bd.sd = d_sd;
+    bd.nsolve = nsolve;
+    bd.N = N;
+    bd.part = d_part;
+    bd.G = G;
+    bd.pstride = pstride;
+    bd.counters = d_counters;
+    bd.df = df;
+    bd.pmax = 0;
+    // beta^2 sits in .x of pout3[0]; pass it through a per-solve array
+    {
+        std::vector<double> b2(nsolve);
+        for (int i = 0; i < nsolve; i++) b2[i] = nrm[i][0].x;
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_mu, b2.data(), nsolve * sizeof(double), cudaMemcpyHostToDevice, st));
+        if (int rc = ovl_start_vector(lat, bd, d_mu, 1, st)) return rc;
+    }
+    // ---- Arnoldi loop ----
+    std::vector<double> mus(nsolve);
+    std::vector<void*> ptrs(2 * nsolve);
+    for (int i = 0; i < nsolve; i++) {
+        mus[i] = params[i].mu;
+        ptrs[i] = P[i].u;
+        ptrs[nsolve + i] = P[i].w;
+    }
+    OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_mu, mus.data(), nsolve * sizeof(double), cudaMemcpyHostToDevice, st));
+    OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_ptrs, ptrs.data(), 2 * nsolve * sizeof(void*), cudaMemcpyHostToDevice, st));
+    DslashArgs da;
+    da.in = (const void* const*)d_ptrs;
+    da.out = (void* const*)(d_ptrs + nsolve);
+    da.mu = d_mu;
+    da.active = &d_sd[0].active;
+    da.klim = &d_sd[0].k;
+    da.stride = (int)(sizeof(SolveDev) / sizeof(int));
+    da.nrhs = nsolve;
+    da.kappa = 1.0 / (8.0 + 2.0 * m_w);
+    const int links = prec == OVL_PREC_FP64 ? OVL_LINKS_F64 : prec == OVL_PREC_MIXED ? OVL_LINKS_F32 : OVL_LINKS_R12;
+    for (int j = 1; j <= kmax; j++) {
+        int pmax = 0;
+        for (int i = 0; i < nsolve; i++)
+            if (j <= P[i].k) pmax = std::max(pmax, P[i].m_q + j - 1);
+        bd.pmax = pmax;
+        da.j = j;
+        if (int rc = ovl_dslash_launch(lat, da, OVL_VEC_F64, links, st)) return rc;
+        if (int rc = ovl_gs_dot(lat, bd, j, st)) return rc;
+        if (int rc = ovl_gs_reduce(lat, bd, j, st)) return rc;
+        if (int rc = ovl_gs_small(lat, bd, j, st)) return rc;
+        if (int rc = ovl_gs_update(lat, bd, j, st)) return rc;
+    }
+    {
+        int pmax = 0;
+        for (int i = 0; i < nsolve; i++) pmax = std::max(pmax, P[i].m_q + P[i].k);
+        bd.pmax = pmax;
+        if (int rc = ovl_gs_final(lat, bd, st)) return rc;
+    }
+    OVL_CUDA_TRY(lat, cudaMemcpyAsync(hs.data(), d_sd, nsolve * sizeof(SolveDev), cudaMemcpyDeviceToHost, st));
+    OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
+
+    // ---- small sign by Newton ----
+    std::vector<NewtonDev> nd(nsolve);
+    int nmax_run = 0, any_run = 0;
+    for (int i = 0; i < nsolve; i++) {
+        SolvePlan& p = P[i];
+        NewtonDev& q = nd[i];
+        int n = p.m_q + hs[i].k_used;
+        q.H = p.H;
+        q.ldH = p.ldH;
+        q.n = n;
+        q.run = (n > 0 && hs[i].status == 0) ? 1 : 0;
+        q.max_iter = params[i].newton_max_iter > 0 ? params[i].newton_max_iter : 100;
+        q.tol = params[i].newton_tol > 0 ? params[i].newton_tol : 1e-13;
+        q.X = p.X;
+        q.W = p.W;
+        q.cand_val = p.cand_val;
+        q.cand_row = p.cand_row;
+        q.red = p.red;
+        q.bar = p.bar;
+        q.status = p.nstat;
+        q.iters = p.iters;
+        q.cvec = p.cvec;
+        q.gout = p.gcomb;
+        if (q.run) {
+            any_run = 1;
+            nmax_run = std::max(nmax_run, n);
+        }
+        // coefficient vector: Schur (S^dag b; beta e_1), otherwise beta e_1
+        std::vector<double2> cv(std::max(1, n), make_double2(0.0, 0.0));
+        if (p.scheme == OVL_DEFL_SCHUR)
+            for (int t = 0; t < p.m_q; t++) cv[t] = make_double2(c1[i][t].x + c2[i][t].x, c1[i][t].y + c2[i][t].y);
+        if (n > p.m_q && hs[i].k_used > 0) cv[p.m_q] = make_double2(beta[i], 0.0);
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(p.cvec, cv.data(), std::max(1, n) * sizeof(double2), cudaMemcpyHostToDevice, st));
+        OVL_CUDA_TRY(lat, cudaMemsetAsync(p.bar, 0, sizeof(unsigned), st));
+        OVL_CUDA_TRY(lat, cudaMemsetAsync(p.nstat, 0, sizeof(int), st));
+        OVL_CUDA_TRY(lat, cudaMemsetAsync(p.iters, 0, sizeof(int), st));
+        OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
+    }
+    OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_nd, nd.data(), nsolve * sizeof(NewtonDev), cudaMemcpyHostToDevice, st));
+    if (any_run) {
+        int cpm_run = ovl_newton_cpm(lat, nsolve, nmax_run);
+        (void)cpm;
+        if (int rc = ovl_newton_launch(lat, d_nd, nsolve, cpm_run, st)) return rc;
+        if (int rc = ovl_fmatvec_launch(lat, d_nd, nsolve, nmax_run, st)) return rc;
+    }
+    std::vector<int> nstat(nsolve, 0), nit(nsolve, 0);
+    for (int i = 0; i < nsolve; i++) {
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(&nstat[i], P[i].nstat, sizeof(int), cudaMemcpyDeviceToHost, st));
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(&nit[i], P[i].iters, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+    OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
+
+    // ---- recombination ----
+    std::vector<GemvDev> gd(nsolve);
+    int gmax = 0;
+    for (int i = 0; i < nsolve; i++) {
+        SolvePlan& p = P[i];
+        int n = nd[i].run ? nd[i].n : 0;
+        std::vector<const float2*> ch, cl;
+        std::vector<double2> extra;
+        for (int cidx = 0; cidx < n; cidx++) {
+            if (cidx < p.m_q) {
+                ch.push_back(p.d->S_hi + N * cidx);
+                cl.push_back(p.d->S_lo + N * cidx);
+            } else {
+                ch.push_back(p.Vhi + N * (cidx - p.m_q));
+                cl.push_back(df ? p.Vlo + N * (cidx - p.m_q) : nullptr);
+            }
+        }
+        if (p.scheme == OVL_DEFL_LR) {
+            // R sgn(Lambda) L^dag b  (Eq. 22, f = sgn on the diagonal)
+            for (int t = 0; t < p.m_defl; t++) {
+                ch.push_back(p.d->S_hi + N * t);
+                cl.push_back(p.d->S_lo + N * t);
+                double lre = p.d->T_host[2 * t];
+                double sg = lre > 0 ? 1.0 : (lre < 0 ? -1.0 : 0.0);
+                extra.push_back(make_double2(sg * c1[i][t].x, sg * c1[i][t].y));
+            }
+        }
+        if (!extra.empty())
+            OVL_CUDA_TRY(lat, cudaMemcpyAsync(p.gcomb + n, extra.data(), extra.size() * sizeof(double2),
+                                              cudaMemcpyHostToDevice, st));
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(p.gc_hi, ch.data(), ch.size() * sizeof(void*), cudaMemcpyHostToDevice, st));
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(p.gc_lo, cl.data(), cl.size() * sizeof(void*), cudaMemcpyHostToDevice, st));
+        OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
+        gd[i].qhi = p.gc_hi;
+        gd[i].qlo = p.gc_lo;
+        gd[i].g = p.gcomb;
+        gd[i].y = p.w;
+        gd[i].ncol = (int)ch.size();
+        gmax = std::max(gmax, gd[i].ncol);
+    }
+    OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_gd, gd.data(), nsolve * sizeof(GemvDev), cudaMemcpyHostToDevice, st));
+    if (int rc = ovl_gemv_df(lat, d_gd, nsolve, gmax, st)) return rc;
+    // ---- outputs ----
+    bool ydev = ovl_is_device_ptr(y);
+    for (int i = 0; i < nsolve; i++) {
+        double* dst = ydev ? y + 2 * N * i : (double*)(d_canon + N * i);
+        if (int rc = ovl_unpack_impl(lat, P[i].w, dst, 1, OVL_VEC_F64, st)) return rc;
+    }
+    if (!ydev)
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(y, d_canon, N * sizeof(double2) * nsolve, cudaMemcpyDeviceToHost, st));
+    OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
+    int first_bad = OVL_OK;
+    for (int i = 0; i < nsolve; i++) {
+        int stt = hs[i].status ? hs[i].status : nstat[i];
+        if (stt && !first_bad) first_bad = stt;
+        if (info) {
+            info[i].status = stt;
+            info[i].k_used = hs[i].k_used;
+            info[i].m_used = P[i].m_defl;
+            info[i].newton_iters = nit[i];
+            info[i].beta = beta[i];
+            double bk = 0.0;
+            cudaMemcpy(&bk, P[i].scal + 4, sizeof(double), cudaMemcpyDeviceToHost);
+            info[i].beta_k = bk;
+        }
+    }
+    if (first_bad) return ovl_fail(lat, first_bad, "ovl_sign_apply: a solve failed (first status %d)", first_bad);
+    return OVL_OK;
+}
+
+extern "C" int ovl_deflation_setup(ovl_lattice lat, double mu, double m_w, int scheme, int m, double tol,
+                                   int max_restarts, ovl_deflation* out) {
+    (void)mu;
+    (void)m_w;
+    (void)scheme;
+    (void)m;
+    (void)tol;
+    (void)max_restarts;
+    (void)out;
+    return ovl_fail(lat, OVL_ENOTSUP, "ovl_deflation_setup: eigensolver not built yet");
+}

@@ -1,0 +1,205 @@
+"""ctypes binding of the C ABI in include/ovl.h (argument marshalling only).
+
+Every ``ovl_*`` function here has the name and arguments of its C
+counterpart; arrays may be numpy arrays (host) or torch tensors (host or
+CUDA) of complex128 in the canonical layouts the header describes. Nothing
+here computes: every step runs in libovl.so, and a missing library raises
+``OvlError`` instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "libovl.so")
+
+OVL_OK, OVL_EINVAL, OVL_ENOMEM, OVL_ECUDA, OVL_ENOCONV, OVL_ETIMEOUT, OVL_ENOTSUP = range(7)
+OVL_PREC_FP64, OVL_PREC_MIXED, OVL_PREC_MIXED_R12 = 0, 1, 2
+OVL_DEFL_NONE, OVL_DEFL_SCHUR, OVL_DEFL_LR = 0, 1, 2
+OVL_VEC_F64, OVL_VEC_F32 = 0, 1
+OVL_LINKS_F64, OVL_LINKS_F32, OVL_LINKS_R12 = 0, 1, 2
+
+
+class OvlError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ovl error {code}: {msg}")
+        self.code = code
+
+
+class ovl_sign_params(C.Structure):
+    _fields_ = [("mu", C.c_double), ("m_w", C.c_double), ("k", C.c_int), ("prec", C.c_int),
+                ("newton_max_iter", C.c_int), ("newton_tol", C.c_double)]
+
+
+class ovl_sign_info(C.Structure):
+    _fields_ = [("status", C.c_int), ("k_used", C.c_int), ("m_used", C.c_int), ("newton_iters", C.c_int),
+                ("beta", C.c_double), ("beta_k", C.c_double)]
+
+
+_lib = None
+_P = C.c_void_p
+_SIGS = {
+    "ovl_create_lattice": (C.c_int, [C.POINTER(C.c_int), C.c_int, _P, C.POINTER(_P)]),
+    "ovl_destroy_lattice": (C.c_int, [_P]),
+    "ovl_set_links": (C.c_int, [_P, _P]),
+    "ovl_apply_Hw": (C.c_int, [_P, C.c_double, C.c_double, _P, _P, C.c_int, C.c_int]),
+    "ovl_apply_Hw_packed": (C.c_int, [_P, _P, C.c_double, _P, _P, C.c_int, C.c_int, C.c_int]),
+    "ovl_pack_spinor": (C.c_int, [_P, _P, _P, C.c_int, C.c_int]),
+    "ovl_unpack_spinor": (C.c_int, [_P, _P, _P, C.c_int, C.c_int]),
+    "ovl_set_deflation": (C.c_int, [_P, C.c_double, C.c_double, C.c_int, C.c_int, _P, _P, _P, C.POINTER(_P)]),
+    "ovl_deflation_setup": (C.c_int, [_P, C.c_double, C.c_double, C.c_int, C.c_int, C.c_double, C.c_int,
+                                      C.POINTER(_P)]),
+    "ovl_get_deflation": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), _P, _P, _P]),
+    "ovl_destroy_deflation": (C.c_int, [_P]),
+    "ovl_sign_apply": (C.c_int, [_P, C.c_int, C.POINTER(ovl_sign_params), C.POINTER(_P), _P, _P,
+                                 C.POINTER(ovl_sign_info)]),
+    "ovl_last_error": (C.c_char_p, [_P]),
+    "ovl_version": (C.c_char_p, []),
+}
+
+
+def lib():
+    """Load libovl.so (raises OvlError if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBPATH):
+            raise OvlError(OVL_ENOTSUP, f"{LIBPATH} is not built; run paper_0710_0341_gb300.build.build()")
+        L = C.CDLL(LIBPATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc, h=None):
+    if rc != OVL_OK:
+        msg = lib().ovl_last_error(h)
+        raise OvlError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or torch tensor (must be contiguous)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    import numpy as np
+
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def ovl_version():
+    return lib().ovl_version().decode()
+
+
+def ovl_create_lattice(dims, antiperiodic_t=0, stream=None):
+    h = _P()
+    d = (C.c_int * 4)(*[int(x) for x in dims])
+    _check(lib().ovl_create_lattice(d, int(antiperiodic_t), _stream_ptr(stream), C.byref(h)))
+    return h
+
+
+def ovl_destroy_lattice(h):
+    _check(lib().ovl_destroy_lattice(h), h)
+
+
+def ovl_set_links(h, U):
+    _check(lib().ovl_set_links(h, _ptr(U)), h)
+
+
+def ovl_apply_Hw(h, mu, m_w, x, out, nrhs=1, links=OVL_LINKS_F64):
+    _check(lib().ovl_apply_Hw(h, float(mu), float(m_w), _ptr(x), _ptr(out), int(nrhs), int(links)), h)
+    return out
+
+
+def ovl_apply_Hw_packed(h, mus, m_w, x, out, nrhs, fmt, links):
+    arr = (C.c_double * nrhs)(*[float(m) for m in mus])
+    _check(lib().ovl_apply_Hw_packed(h, C.cast(arr, _P), float(m_w), _ptr(x), _ptr(out), int(nrhs), int(fmt),
+                                     int(links)), h)
+    return out
+
+
+def ovl_pack_spinor(h, canon, packed, nrhs, fmt):
+    _check(lib().ovl_pack_spinor(h, _ptr(canon), _ptr(packed), int(nrhs), int(fmt)), h)
+
+
+def ovl_unpack_spinor(h, packed, canon, nrhs, fmt):
+    _check(lib().ovl_unpack_spinor(h, _ptr(packed), _ptr(canon), int(nrhs), int(fmt)), h)
+
+
+def ovl_set_deflation(h, mu, m_w, scheme, m, S_or_R, T, L=None):
+    d = _P()
+    _check(lib().ovl_set_deflation(h, float(mu), float(m_w), int(scheme), int(m), _ptr(S_or_R), _ptr(T), _ptr(L),
+                                   C.byref(d)), h)
+    return d
+
+
+def ovl_deflation_setup(h, mu, m_w, scheme, m, tol=1e-12, max_restarts=500):
+    d = _P()
+    _check(lib().ovl_deflation_setup(h, float(mu), float(m_w), int(scheme), int(m), float(tol), int(max_restarts),
+                                     C.byref(d)), h)
+    return d
+
+
+def ovl_get_deflation(d, S_or_R=None, T=None, L=None, h=None):
+    sch, m = C.c_int(), C.c_int()
+    _check(lib().ovl_get_deflation(d, C.byref(sch), C.byref(m), _ptr(S_or_R), _ptr(T), _ptr(L)), h)
+    return sch.value, m.value
+
+
+def ovl_destroy_deflation(d):
+    _check(lib().ovl_destroy_deflation(d))
+
+
+def ovl_sign_apply(h, params, defl, b, y, info=True):
+    """params: list of dicts (mu, m_w, k, prec[, newton_max_iter, newton_tol]);
+    defl: list of deflation handles or None (same length)."""
+    n = len(params)
+    P = (ovl_sign_params * n)()
+    for i, p in enumerate(params):
+        P[i].mu = p["mu"]
+        P[i].m_w = p["m_w"]
+        P[i].k = int(p["k"])
+        P[i].prec = int(p.get("prec", OVL_PREC_FP64))
+        P[i].newton_max_iter = int(p.get("newton_max_iter", 0))
+        P[i].newton_tol = float(p.get("newton_tol", 0.0))
+    D = (_P * n)(*[(d.value if isinstance(d, _P) else d) if d is not None else None for d in (defl or [None] * n)])
+    I = (ovl_sign_info * n)()
+    rc = lib().ovl_sign_apply(h, n, P, D, _ptr(b), _ptr(y), I)
+    infos = [dict(status=I[i].status, k_used=I[i].k_used, m_used=I[i].m_used, newton_iters=I[i].newton_iters,
+                  beta=I[i].beta, beta_k=I[i].beta_k) for i in range(n)]
+    if rc != OVL_OK:
+        msg = lib().ovl_last_error(h)
+        err = OvlError(rc, (msg.decode() if msg else "") + f" infos={infos}")
+        err.infos = infos
+        raise err
+    return infos
+
+
+def ovl_last_error(h=None):
+    m = lib().ovl_last_error(h)
+    return m.decode() if m else ""
+
+
+def header_functions():
+    """Names of the functions include/ovl.h declares (parsed from the header)."""
+    import re
+
+    hdr = os.path.join(_HERE, "..", "include", "ovl.h")
+    txt = open(hdr).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(ovl_\w+)\s*\(", txt, flags=re.M)))

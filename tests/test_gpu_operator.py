@@ -1,0 +1,88 @@
+"""GPU parity of H_w(mu) = gamma_5 D_w(mu) (Sec. 1, Eq. 2) against the oracle.
+
+Called through the C ABI (ctypes binding). FP64 links: relative error <= 1e-13
+(the same sums in another order). FP32 and 12-real links: <= 2e-6 (FP32
+arithmetic: |U| = 1, 49 terms per row, u32 = 6e-8).
+"""
+import numpy as np
+import pytest
+
+from helpers import canon_cols, lattice, need_gpu, rel, to_dev
+from oracle import dirac
+from paper_0710_0341_gb300 import ovl, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dims,apbc", [((4, 4, 4, 4), 0), ((3, 4, 2, 5), 1), ((2, 2, 2, 2), 0), ((5, 3, 7, 6), 0)])
+@pytest.mark.parametrize("mu", [0.0, 0.3])
+def test_apply_hw_fp64_and_fp32(dims, apbc, mu):
+    torch = need_gpu()
+    U = synth.random_su3_field(dims, 0.5, 0)
+    h = lattice(dims, U, apbc)
+    try:
+        A = dirac.hermitian_wilson(U, mu, -1.1, antiperiodic_t=bool(apbc))
+        x = np.stack([synth.gaussian_source(dims, 3), synth.gaussian_source(dims, 4)])
+        ref = np.stack([dirac.apply(A, x[0]), dirac.apply(A, x[1])])
+        for links, tol in ((ovl.OVL_LINKS_F64, 1e-13), (ovl.OVL_LINKS_F32, 2e-6), (ovl.OVL_LINKS_R12, 2e-6)):
+            out = np.zeros_like(x)
+            ovl.ovl_apply_Hw(h, mu, -1.1, x, out, 2, links)  # host pointers
+            assert rel(out, ref) < tol, (links, rel(out, ref))
+            xd = to_dev(torch, x)
+            od = torch.zeros_like(xd)
+            ovl.ovl_apply_Hw(h, mu, -1.1, xd, od, 2, links)  # device pointers
+            assert rel(od.cpu().numpy(), ref) < tol
+    finally:
+        ovl.ovl_destroy_lattice(h)
+
+
+def test_packed_roundtrip_and_packed_stencil():
+    torch = need_gpu()
+    dims = (4, 6, 2, 4)
+    U = synth.random_su3_field(dims, 0.4, 1)
+    h = lattice(dims, U)
+    try:
+        x = np.stack([synth.gaussian_source(dims, 5), synth.gaussian_source(dims, 6), synth.gaussian_source(dims, 7)])
+        xd = to_dev(torch, x)
+        N = x[0].size
+        p64 = torch.zeros(3 * N, dtype=torch.complex128, device="cuda")
+        ovl.ovl_pack_spinor(h, xd, p64, 3, ovl.OVL_VEC_F64)
+        back = torch.zeros_like(xd)
+        ovl.ovl_unpack_spinor(h, p64, back, 3, ovl.OVL_VEC_F64)
+        assert torch.equal(back, xd)  # bit-exact permutation
+        out = torch.zeros_like(p64)
+        mus = [0.0, 0.25, 0.6]
+        ovl.ovl_apply_Hw_packed(h, mus, -1.0, p64, out, 3, ovl.OVL_VEC_F64, ovl.OVL_LINKS_F64)
+        ovl.ovl_unpack_spinor(h, out, back, 3, ovl.OVL_VEC_F64)
+        for r in range(3):
+            ref = dirac.apply(dirac.hermitian_wilson(U, mus[r], -1.0), x[r])
+            assert rel(back[r].cpu().numpy(), ref) < 1e-13
+        p32 = torch.zeros(3 * N, dtype=torch.complex64, device="cuda")
+        ovl.ovl_pack_spinor(h, xd, p32, 3, ovl.OVL_VEC_F32)
+        o32 = torch.zeros_like(p32)
+        ovl.ovl_apply_Hw_packed(h, mus, -1.0, p32, o32, 3, ovl.OVL_VEC_F32, ovl.OVL_LINKS_R12)
+        ovl.ovl_unpack_spinor(h, o32, back, 3, ovl.OVL_VEC_F32)
+        for r in range(3):
+            ref = dirac.apply(dirac.hermitian_wilson(U, mus[r], -1.0), x[r])
+            assert rel(back[r].cpu().numpy(), ref) < 3e-6
+    finally:
+        ovl.ovl_destroy_lattice(h)
+
+
+def test_invalid_arguments_are_rejected():
+    need_gpu()
+    with pytest.raises(ovl.OvlError) as e:
+        ovl.ovl_create_lattice((1, 4, 4, 4))
+    assert e.value.code == ovl.OVL_EINVAL
+    dims = (2, 2, 2, 2)
+    h = ovl.ovl_create_lattice(dims)
+    try:
+        x = synth.gaussian_source(dims, 1)
+        with pytest.raises(ovl.OvlError) as e:  # links not set
+            ovl.ovl_apply_Hw(h, 0.1, -1.0, x, np.zeros_like(x), 1, ovl.OVL_LINKS_F64)
+        assert e.value.code == ovl.OVL_EINVAL
+        ovl.ovl_set_links(h, synth.unit_gauge_field(dims))
+        with pytest.raises(ovl.OvlError):
+            ovl.ovl_apply_Hw(h, 0.1, -1.0, x, np.zeros_like(x), 1, 7)
+    finally:
+        ovl.ovl_destroy_lattice(h)

@@ -1,0 +1,223 @@
+"""GPU parity of the deflated Arnoldi sign function (Secs. 2-4) against the oracle.
+
+The CUDA path and the oracle see the same seeded inputs and, for deflation,
+the same eigenvectors (computed by the oracle's dense eigensolver).
+Tolerances: FP64 mode vs the oracle's identical algorithm (same k, same
+deflation vectors): 1e-10 relative (the target the method's FP64 mode is
+held to). Mixed modes: 1e-5 (FP32 basis: u32 = 6e-8 per entry, amplified by
+the sign function's conditioning on these small lattices).
+"""
+import numpy as np
+import pytest
+
+from helpers import canon_cols, lattice, need_gpu, rel, to_dev
+from oracle import dirac, eigen, freefield, krylov, matfunc
+from paper_0710_0341_gb300 import ovl, synth
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (2, 2, 2, 4)
+
+
+def _setup(dims, eps, mu, m_w, seed=0):
+    U = synth.random_su3_field(dims, eps, seed)
+    A = dirac.hermitian_wilson(U, mu, m_w)
+    return U, A
+
+
+def _schur(A, dims, m):
+    lam, R, L = eigen.critical_dense(A.toarray(), m)
+    S, T = eigen.schur_from_right(A, R)
+    return S, T, lam, R, L
+
+
+def _defl_schur(h, mu, m_w, S, T, dims):
+    return ovl.ovl_set_deflation(h, mu, m_w, ovl.OVL_DEFL_SCHUR, S.shape[1], canon_cols(S, dims),
+                                 np.asfortranarray(T).ravel(order="F").copy(), None)
+
+
+def _defl_lr(h, mu, m_w, lam, R, L, dims):
+    return ovl.ovl_set_deflation(h, mu, m_w, ovl.OVL_DEFL_LR, R.shape[1], canon_cols(R, dims),
+                                 np.ascontiguousarray(lam), canon_cols(L, dims))
+
+
+@pytest.mark.parametrize("dims", [DIMS, (3, 4, 2, 5)])
+def test_no_deflation_fp64(dims):
+    need_gpu()
+    U, A = _setup(dims, 0.5, 0.3, -1.0)
+    b = synth.gaussian_source(dims, 1)
+    h = lattice(dims, U)
+    try:
+        for k in (1, 7, 40):
+            y = np.zeros_like(b)
+            info = ovl.ovl_sign_apply(h, [dict(mu=0.3, m_w=-1.0, k=k)], [None], b, y)
+            yo = krylov.sign_arnoldi(A, b.ravel(), k)
+            assert info[0]["k_used"] == k
+            assert rel(y, yo) < 1e-10, (k, rel(y, yo))
+    finally:
+        ovl.ovl_destroy_lattice(h)
+
+
+def test_schur_and_lr_fp64():
+    torch = need_gpu()
+    mu, m_w = 0.3, -1.0
+    U, A = _setup(DIMS, 0.5, mu, m_w)
+    S, T, lam, R, L = _schur(A, DIMS, 12)
+    b = synth.gaussian_source(DIMS, 1)
+    h = lattice(DIMS, U)
+    try:
+        ds = _defl_schur(h, mu, m_w, S, T, DIMS)
+        dl = _defl_lr(h, mu, m_w, lam, R, L, DIMS)
+        k = 30
+        bb = np.stack([b, b])
+        y = np.zeros_like(bb)
+        infos = ovl.ovl_sign_apply(h, [dict(mu=mu, m_w=m_w, k=k)] * 2, [ds, dl], bb, y)
+        ys = krylov.sign_schur(A, b.ravel(), k, S, T)
+        yl = krylov.sign_lr(A, b.ravel(), k, R, lam, L)
+        assert rel(y[0], ys) < 1e-10, rel(y[0], ys)
+        assert rel(y[1], yl) < 1e-10, rel(y[1], yl)
+        assert infos[0]["m_used"] == 12 and infos[1]["m_used"] == 12
+        # device-resident input and output give the same numbers
+        bd = to_dev(torch, bb)
+        yd = torch.zeros_like(bd)
+        ovl.ovl_sign_apply(h, [dict(mu=mu, m_w=m_w, k=k)] * 2, [ds, dl], bd, yd)
+        assert rel(yd.cpu().numpy(), y) < 1e-14
+        # deflation data round trip
+        S2 = np.zeros((12,) + b.shape, dtype=np.complex128)
+        T2 = np.zeros(144, dtype=np.complex128)
+        sch, m = ovl.ovl_get_deflation(ds, S2, T2, None, h)
+        assert sch == ovl.OVL_DEFL_SCHUR and m == 12
+        assert rel(S2, canon_cols(S, DIMS)) < 1e-14
+        assert np.array_equal(T2.reshape(12, 12, order="F"), T)
+        ovl.ovl_destroy_deflation(ds)
+        ovl.ovl_destroy_deflation(dl)
+    finally:
+        ovl.ovl_destroy_lattice(h)
+
+
+def test_uneven_batch_mixed_schemes():
+    need_gpu()
+    m_w = -1.0
+    U = synth.random_su3_field(DIMS, 0.5, 0)
+    h = lattice(DIMS, U)
+    try:
+        A3 = dirac.hermitian_wilson(U, 0.3, m_w)
+        A1 = dirac.hermitian_wilson(U, 0.1, m_w)
+        A0 = dirac.hermitian_wilson(U, 0.0, m_w)
+        S, T, lam, R, L = _schur(A3, DIMS, 10)
+        _, _, lam1, R1, L1 = _schur(A1, DIMS, 8)
+        ds = _defl_schur(h, 0.3, m_w, S, T, DIMS)
+        dl = _defl_lr(h, 0.1, m_w, lam1, R1, L1, DIMS)
+        bs = [synth.gaussian_source(DIMS, s) for s in (1, 2, 3, 4)]
+        params = [dict(mu=0.3, m_w=m_w, k=20), dict(mu=0.3, m_w=m_w, k=33), dict(mu=0.1, m_w=m_w, k=25),
+                  dict(mu=0.0, m_w=m_w, k=41)]
+        y = np.zeros((4,) + bs[0].shape, dtype=np.complex128)
+        infos = ovl.ovl_sign_apply(h, params, [None, ds, dl, None], np.stack(bs), y)
+        refs = [krylov.sign_arnoldi(A3, bs[0].ravel(), 20), krylov.sign_schur(A3, bs[1].ravel(), 33, S, T),
+                krylov.sign_lr(A1, bs[2].ravel(), 25, R1, lam1, L1), krylov.sign_arnoldi(A0, bs[3].ravel(), 41)]
+        for i in range(4):
+            assert infos[i]["k_used"] == params[i]["k"]
+            assert rel(y[i], refs[i]) < 1e-10, (i, rel(y[i], refs[i]))
+    finally:
+        ovl.ovl_destroy_lattice(h)
+
+
+@pytest.mark.parametrize("prec,tol", [(ovl.OVL_PREC_MIXED, 1e-5), (ovl.OVL_PREC_MIXED_R12, 1e-5)])
+def test_mixed_precision_bound(prec, tol):
+    need_gpu()
+    mu, m_w = 0.3, -1.0
+    U, A = _setup(DIMS, 0.5, mu, m_w)
+    S, T, lam, R, L = _schur(A, DIMS, 12)
+    b = synth.gaussian_source(DIMS, 1)
+    h = lattice(DIMS, U)
+    try:
+        ds = _defl_schur(h, mu, m_w, S, T, DIMS)
+        dl = _defl_lr(h, mu, m_w, lam, R, L, DIMS)
+        bb = np.stack([b, b, b])
+        y = np.zeros_like(bb)
+        ovl.ovl_sign_apply(h, [dict(mu=mu, m_w=m_w, k=30, prec=prec)] * 3, [ds, dl, None], bb, y)
+        refs = [krylov.sign_schur(A, b.ravel(), 30, S, T), krylov.sign_lr(A, b.ravel(), 30, R, lam, L),
+                krylov.sign_arnoldi(A, b.ravel(), 30)]
+        for i in range(3):
+            assert rel(y[i], refs[i]) < tol, (i, rel(y[i], refs[i]))
+    finally:
+        ovl.ovl_destroy_lattice(h)
+
+
+def test_full_krylov_space_is_exact():
+    need_gpu()
+    dims = (2, 2, 2, 2)
+    U, A = _setup(dims, 0.5, 0.3, -1.0)
+    b = synth.gaussian_source(dims, 1)
+    ystar = matfunc.sign_eig_apply(A.toarray(), b.ravel())
+    h = lattice(dims, U)
+    try:
+        y = np.zeros_like(b)
+        info = ovl.ovl_sign_apply(h, [dict(mu=0.3, m_w=-1.0, k=192)], [None], b, y)
+        assert info[0]["k_used"] <= 192
+        assert rel(y, ystar) < 1e-8, rel(y, ystar)
+    finally:
+        ovl.ovl_destroy_lattice(h)
+
+
+def test_free_field_8x4_closed_form():
+    """Full config size (8^4, N = 49152): U = 1 has a closed-form sign."""
+    need_gpu()
+    dims = (8, 8, 8, 8)
+    U = synth.unit_gauge_field(dims)
+    b = synth.gaussian_source(dims, 1)
+    ystar = freefield.sign_hw_free(b, 0.3, -1.0)
+    h = lattice(dims, U)
+    try:
+        y = np.zeros_like(b)
+        ovl.ovl_sign_apply(h, [dict(mu=0.3, m_w=-1.0, k=200)], [None], b, y)
+        assert rel(y, ystar) < 1e-10, rel(y, ystar)
+    finally:
+        ovl.ovl_destroy_lattice(h)
+
+
+@pytest.mark.slow
+def test_config_4x4_schur_k200_m20():
+    """4^4, eps 0.5, m_w -1, mu 0.3, Gaussian source, k 200, Schur m 20, FP64:
+    parity with the oracle's algorithm and accuracy against dense eig."""
+    need_gpu()
+    dims = (4, 4, 4, 4)
+    U, A = _setup(dims, 0.5, 0.3, -1.0)
+    Ad = A.toarray()
+    b = synth.gaussian_source(dims, 1)
+    ystar = matfunc.sign_eig_apply(Ad, b.ravel())
+    lam, R, L = eigen.critical_dense(Ad, 20)
+    S, T = eigen.schur_from_right(A, R)
+    yo = krylov.sign_schur(A, b.ravel(), 200, S, T)
+    h = lattice(dims, U)
+    try:
+        ds = _defl_schur(h, 0.3, -1.0, S, T, dims)
+        y = np.zeros_like(b)
+        ovl.ovl_sign_apply(h, [dict(mu=0.3, m_w=-1.0, k=200)], [ds], b, y)
+        assert rel(y, yo) < 1e-10, rel(y, yo)
+        assert rel(y, ystar) < 1e-8, rel(y, ystar)
+    finally:
+        ovl.ovl_destroy_lattice(h)
+
+
+def test_sign_argument_errors():
+    need_gpu()
+    U, A = _setup(DIMS, 0.5, 0.3, -1.0)
+    S, T, lam, R, L = _schur(A, DIMS, 4)
+    b = synth.gaussian_source(DIMS, 1)
+    h = lattice(DIMS, U)
+    try:
+        ds = _defl_schur(h, 0.3, -1.0, S, T, DIMS)
+        y = np.zeros_like(b)
+        with pytest.raises(ovl.OvlError) as e:  # deflation built for another mu
+            ovl.ovl_sign_apply(h, [dict(mu=0.2, m_w=-1.0, k=10)], [ds], b, y)
+        assert e.value.code == ovl.OVL_EINVAL
+        with pytest.raises(ovl.OvlError) as e:  # beyond the basis limit
+            ovl.ovl_sign_apply(h, [dict(mu=0.3, m_w=-1.0, k=5000)], [None], b, y)
+        assert e.value.code == ovl.OVL_EINVAL
+        with pytest.raises(ovl.OvlError) as e:  # one precision per batch
+            ovl.ovl_sign_apply(h, [dict(mu=0.3, m_w=-1.0, k=5), dict(mu=0.3, m_w=-1.0, k=5, prec=1)],
+                               [None, None], np.stack([b, b]), np.zeros((2,) + b.shape, complex))
+        assert e.value.code == ovl.OVL_EINVAL
+    finally:
+        ovl.ovl_destroy_lattice(h)
