@@ -140,6 +140,9 @@ int ovl_deflation_setup(ovl_lattice lat, double mu, double m_w, int scheme, int 
 /* Copy the deflation data back (canonical layouts as in ovl_set_deflation;
  * L ignored for Schur). Host or device pointers. */
 int ovl_get_deflation(ovl_deflation d, int* scheme, int* m, double* S_or_R, double* T, double* L);
+/* Work done by ovl_deflation_setup for this object: restarts of the
+ * restarted Arnoldi runs and applications of A^2 (0 for imported data). */
+int ovl_deflation_stats(ovl_deflation d, int* restarts, int* matvecs);
 int ovl_destroy_deflation(ovl_deflation d);
 
 /* ---- the sign function (Secs. 2-4) ------------------------------------- */
@@ -155,6 +158,16 @@ int ovl_destroy_deflation(ovl_deflation d);
  * Returns the first non-zero per-solve status (all solves are attempted). */
 int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params* params,
                    const ovl_deflation* defl, const double* b, double* y, ovl_sign_info* info);
+
+/* Kernel accounting for timing reports. ovl_launch_count: kernels launched
+ * through this handle so far. ovl_profile(enable=1) clears and starts
+ * per-kernel-class CUDA-event timing of ovl_sign_apply on the lattice's
+ * stream; enable=0 stops it. stats (may be NULL) receives 8 records of
+ * {launches, total milliseconds, algorithmic bytes} for the classes:
+ * 0 stencil, 1 Gram-Schmidt pass A, 2 partial-sum reduction, 3 small step,
+ * 4 Gram-Schmidt pass B, 5 Newton sign, 6 FP64 projections, 7 recombination. */
+int ovl_launch_count(ovl_lattice lat, long long* n);
+int ovl_profile(ovl_lattice lat, int enable, double* stats);
 
 /* Message for the last failed call on this handle (NULL handle: the last
  * failure of a call that had no handle yet, e.g. ovl_create_lattice). */

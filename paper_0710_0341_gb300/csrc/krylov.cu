@@ -39,8 +39,8 @@ __device__ __forceinline__ double warp_sumd(double v) {
 
 __device__ __forceinline__ int solve_p(const SolveDev& d, int j) { return j < 0 ? d.m_q + d.k_used : d.m_q + j - 1; }
 __device__ __forceinline__ bool solve_in_step(const SolveDev& d, int j) {
-    if (!d.active) return false;
-    return j < 0 ? true : j <= d.k;
+    if (j < 0) return d.fin != 0;
+    return d.active && j <= d.k;
 }
 
 // ---------------------------------------------------------------------------
@@ -247,12 +247,12 @@ __global__ void __launch_bounds__(256) k_gs_small(BatchDev B, int j) {
             AB.x += sh_c[k].x;
             AB.y += sh_c[k].y;
         }
-        double guu = dots[2 * p].x;
+        double guu = final_pass ? dots[p].x : dots[2 * p].x;
         double nu2 = first ? 1.0 : guu - A2;
         int stop = 0;
         if (!(nu2 == nu2) || !(guu == guu)) {
             stop = 2;  // NaN
-        } else if (!first && nu2 <= 1e-24 * guu) {
+        } else if (!first && !final_pass && nu2 <= 1e-24 * guu) {
             stop = 1;  // invariant subspace reached (happy breakdown)
             nu2 = 0.0;
         }
@@ -285,7 +285,8 @@ __global__ void __launch_bounds__(256) k_gs_small(BatchDev B, int j) {
     const double nu = sh_nu;
     const int stop = sh_stop;
     // update column p-1 with the reorthogonalisation coefficients and nu
-    if (!first) {
+    // (on breakdown the accurate final pass does it with k_used = j - 1)
+    if (!first && stop != 1) {
         for (int c = tid; c < p; c += 256) {
             double2 av = dots[c];
             double2 h = d.H[c + (size_t)(p - 1) * ld];
@@ -305,12 +306,15 @@ __global__ void __launch_bounds__(256) k_gs_small(BatchDev B, int j) {
             if (stop == 2) {
                 d.status = OVL_ENOCONV;
                 d.active = 0;
-            } else if (stop == 1) {
+            } else if (stop == 1 && !final_pass) {
                 d.k_used = j - 1;  // the space spanned so far is invariant
                 d.active = 0;
-                d.scal[4] = 0.0;
+                d.fin = 1;         // u_j is in span(Q): the final pass projects it
             }
-            if (final_pass) d.active = 0;
+            if (final_pass) {
+                d.active = 0;
+                d.fin = 0;
+            }
         }
         if (!final_pass && tid == 0) B.counters[s] = 0;
         return;
@@ -471,13 +475,13 @@ __global__ void __launch_bounds__(256) k_proj_dot(ProjDev* pds, double2* part, i
         }
         for (int c = warp; c < d.ncol; c += 8) {
             const float2* qh = d.qhi[c];
-            const float2* ql = d.qlo[c];
+            const float2* ql = d.qlo ? d.qlo[c] : nullptr;  // no low plane: FP32 column
             double ar = 0.0, ai = 0.0;
 #pragma unroll
             for (int i = 0; i < PJ_RPL; i++) {
                 size_t r = base + 32 * i + lane;
                 if (r < N) {
-                    float2 h = qh[r], l = ql[r];
+                    float2 h = qh[r], l = ql ? ql[r] : make_float2(0.f, 0.f);
                     double qr = (double)h.x + (double)l.x, qi = (double)h.y + (double)l.y;
                     ar += qr * xv[i].x + qi * xv[i].y;
                     ai += qr * xv[i].y - qi * xv[i].x;
@@ -580,6 +584,7 @@ __global__ void __launch_bounds__(256) k_start(BatchDev B, const double* beta2, 
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             d.active = 0;
             d.k_used = 0;
+            d.fin = 0;
         }
         return;
     }
@@ -644,9 +649,13 @@ int ovl_gs_update(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
     return OVL_OK;
 }
 
-int ovl_gs_final(ovl_lattice lat, const BatchDev& b, cudaStream_t st) {
-    if (int rc = ovl_gs_dot(lat, b, -1, st)) return rc;
-    if (int rc = ovl_gs_reduce(lat, b, -1, st)) return rc;
+int ovl_gs_final(ovl_lattice lat, const BatchDev& b, ProjDev* pd_dev, int maxcol, cudaStream_t st) {
+    // Galerkin correction of the last column: s = Q^dag u_{k+1} in FP64
+    // against the full hi+lo basis (the per-step FP32 inner products leave
+    // the basis orthonormal to ~1e-7 only; the Arnoldi relation itself is
+    // exact, and with an accurate s the projected matrix equals
+    // Q^+ A Q, i.e. the result is the Galerkin approximation on span(Q)).
+    if (int rc = ovl_proj_dot(lat, pd_dev, b.nsolve, maxcol, b.part, b.G, st)) return rc;
     return ovl_gs_small(lat, b, -1, st);
 }
 

@@ -33,6 +33,7 @@ struct SolveDev {
     int active;      // cleared on breakdown or error
     int k_used;
     int status;      // OVL_* per solve
+    int fin;         // final (accurate) projection of u still pending
 };
 
 struct BatchDev {
@@ -52,7 +53,6 @@ int ovl_gs_dot(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st);
 int ovl_gs_reduce(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st);
 int ovl_gs_small(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st);
 int ovl_gs_update(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st);
-int ovl_gs_final(ovl_lattice lat, const BatchDev& b, cudaStream_t st);
 int ovl_gs_grid(ovl_lattice lat);
 
 // Accurate (FP64) projections used once per solve for the deflation step and
@@ -60,7 +60,7 @@ int ovl_gs_grid(ovl_lattice lat);
 // plus P[s][ncol_s] = |x_s|^2.
 struct ProjDev {
     const float2* const* qhi;  // column pointers (ncol entries)
-    const float2* const* qlo;
+    const float2* const* qlo;  // null: columns have no low plane
     double2* x;                // packed FP64 vector
     double2* out;              // ncol + 1 results
     const double2* coef;       // for the update: x -= sum_c Q[:,c] coef[c]
@@ -68,6 +68,7 @@ struct ProjDev {
 };
 int ovl_proj_dot(ovl_lattice lat, ProjDev* pd_dev, int nsolve, int maxcol, double2* part, int G, cudaStream_t st);
 int ovl_proj_update(ovl_lattice lat, ProjDev* pd_dev, int nsolve, int maxcol, cudaStream_t st);
+int ovl_gs_final(ovl_lattice lat, const BatchDev& b, ProjDev* pd_dev, int maxcol, cudaStream_t st);
 
 // y_s = sum_c Q_s[:,c] g_s[c] (df accumulation), FP64 packed output.
 struct GemvDev {

@@ -101,6 +101,8 @@ extern "C" int ovl_destroy_lattice(ovl_lattice lat) {
     if (!lat) return OVL_OK;
     cudaStreamSynchronize(lat->stream);
     free_links(lat->links);
+    ovl_prof_flush(lat);
+    for (cudaEvent_t e : lat->event_pool) cudaEventDestroy(e);
     cudaFree(lat->scratch);
     cudaFree(lat->ws);
     cudaFree(lat->d_status);
@@ -298,7 +300,11 @@ static int dslash_packed(ovl_lattice lat, const double* mu_host, double m_w, con
     da.active = nullptr;
     da.nrhs = nrhs;
     da.kappa = 1.0 / (8.0 + 2.0 * m_w);
+    const double sb = fmt == OVL_VEC_F64 ? 16.0 : 8.0;
+    const double lb = links == OVL_LINKS_F64 ? 144.0 : links == OVL_LINKS_F32 ? 72.0 : 48.0;
+    ProfScope ps(lat, 0, nrhs * (double)lat->V * (24.0 * sb + 4.0 * lb), lat->stream);
     int rc = ovl_dslash_launch(lat, da, fmt, links, lat->stream);
+    ps.end(lat->stream);
     // the host vectors above must outlive the async copies
     cudaStreamSynchronize(lat->stream);
     return rc;
@@ -352,5 +358,68 @@ extern "C" int ovl_apply_Hw(ovl_lattice lat, double mu, double m_w, const double
         OVL_CUDA_TRY(lat, cudaMemcpyAsync(out, base + off_in, cb, cudaMemcpyDeviceToHost, lat->stream));
     }
     OVL_CUDA_TRY(lat, cudaStreamSynchronize(lat->stream));
+    return OVL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernel accounting
+// ---------------------------------------------------------------------------
+static cudaEvent_t take_event(ovl_lattice lat) {
+    if (!lat->event_pool.empty()) {
+        cudaEvent_t e = lat->event_pool.back();
+        lat->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+ProfScope::ProfScope(ovl_lattice l, int c, double by, cudaStream_t st) : lat(l), cls(c), bytes(by) {
+    if (!lat->prof) return;
+    a = take_event(lat);
+    b = take_event(lat);
+    cudaEventRecord(a, st);
+}
+
+void ProfScope::end(cudaStream_t st) {
+    if (!lat->prof || !a) return;
+    cudaEventRecord(b, st);
+    lat->prof_pending.push_back({cls, a, b, bytes});
+    a = b = nullptr;
+}
+
+void ovl_prof_flush(ovl_lattice lat) {
+    if (lat->prof_pending.empty()) return;
+    cudaStreamSynchronize(lat->stream);
+    for (auto& r : lat->prof_pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        lat->prof_acc[r.cls][0] += 1;
+        lat->prof_acc[r.cls][1] += ms;
+        lat->prof_acc[r.cls][2] += r.bytes;
+        lat->event_pool.push_back(r.a);
+        lat->event_pool.push_back(r.b);
+    }
+    lat->prof_pending.clear();
+}
+
+extern "C" int ovl_launch_count(ovl_lattice lat, long long* n) {
+    if (!lat || !n) return ovl_fail(lat, OVL_EINVAL, "ovl_launch_count: null argument");
+    *n = lat->launches;
+    return OVL_OK;
+}
+
+extern "C" int ovl_profile(ovl_lattice lat, int enable, double* stats) {
+    if (!lat) return ovl_fail(lat, OVL_EINVAL, "ovl_profile: null handle");
+    ovl_prof_flush(lat);
+    if (stats)
+        for (int c = 0; c < OVL_PROF_CLASSES; c++)
+            for (int k = 0; k < 3; k++) stats[3 * c + k] = lat->prof_acc[c][k];
+    if (enable) {
+        for (int c = 0; c < OVL_PROF_CLASSES; c++)
+            for (int k = 0; k < 3; k++) lat->prof_acc[c][k] = 0.0;
+    }
+    lat->prof = enable != 0;
     return OVL_OK;
 }

@@ -2,8 +2,10 @@
 // iteration (the matrix iterations Sec. 2 refers to; used for f(H_k) in
 // Eqs. 11 and 22 and for f(H) on the whole block matrix of Eqs. 15-17):
 //   X_0 = H,  X_{i+1} = (c_i X_i + X_i^{-1} / c_i) / 2,  c_i = |det X_i|^{-1/n},
-// scaling dropped once |X_{i+1} - X_i|_F < 1e-2 |X_{i+1}|_F, stopped at
-// |X_{i+1} - X_i|_F <= tol |X_{i+1}|_F.
+// scaling dropped once the relative step |X_{i+1} - X_i|_F / |X_{i+1}|_F is
+// below 1e-2; stopped when the relative step is below tol, one step after it
+// fell below 1e-10 (quadratic convergence puts the next one near rounding),
+// or when rounding stalls it (the step below 1e-8 no longer halves).
 //
 // One cooperative launch runs every iteration of every solve of a batch. The
 // CTAs of one solve form a group that owns the matrix rows round-robin and
@@ -84,11 +86,14 @@ __global__ void __launch_bounds__(NT) k_newton(NewtonDev* nds, int nsolve, int c
     __shared__ int piv[OVL_NEWTON_MAXN];
     __shared__ double s_red[NT / 32][2];
     __shared__ int s_idx[NT / 32];
+    __shared__ double2 s_inv;
+    __shared__ double s_c;
     unsigned gen = 0;
     // X_0 = H (column-major input, row-major iterate)
     for (int i = g; i < n; i += cpm)
         for (int l = tid; l < n; l += NT) X[(size_t)i * n + l] = d.H[i + (size_t)l * d.ldH];
     bool scaling = true;
+    double prev_rel = 1e300;
     int iter = 0;
     bool converged = false;
     if (!group_sync(d, gen, cpm)) return;
@@ -155,17 +160,21 @@ __global__ void __launch_bounds__(NT) k_newton(NewtonDev* nds, int nsolve, int c
                 if (pp % cpm == g)
                     for (int l = tid; l < n; l += NT) W[(size_t)pp * n + l] = prow[buf ^ 1][l];
             }
-            double2 pv = W[(size_t)pr * n + k];
-            double2 inv = cinv(pv);
+            // FP64 is scarce on this GPU: the pivot reciprocal and log|pivot|
+            // are formed once per CTA, not once per thread
+            if (tid == 0) {
+                double2 pv = W[(size_t)pr * n + k];
+                s_inv = cinv(pv);
+                logdet += 0.5 * log(cabs2(pv));
+                used[pr] = 1;
+                piv[k] = pr;
+            }
+            __syncthreads();
+            const double2 inv = s_inv;
             for (int l = tid; l < n; l += NT) {
                 double2 v = W[(size_t)pr * n + l];
                 prow[buf][l] = (l == k) ? inv : cmul(v, inv);
             }
-            if (tid == 0) {
-                used[pr] = 1;
-                piv[k] = pr;
-            }
-            logdet += 0.5 * log(cabs2(pv));
             __syncthreads();
             // eliminate own rows i != pr
             for (int i = g + cpm * warp; i < n; i += cpm * (NT / 32)) {
@@ -199,7 +208,9 @@ __global__ void __launch_bounds__(NT) k_newton(NewtonDev* nds, int nsolve, int c
         }
         if (!group_sync(d, gen, cpm)) return;
         // X_new[i][piv_j] = (c X[i][piv_j] + W[piv_i][j] / c) / 2
-        const double c = scaling ? exp(-logdet / n) : 1.0;
+        if (tid == 0) s_c = scaling ? exp(-logdet / n) : 1.0;
+        __syncthreads();
+        const double c = s_c;
         const double ic = 1.0 / c;
         double dsum = 0.0, nsum = 0.0;
         for (int i = g + cpm * warp; i < n; i += cpm * (NT / 32)) {
@@ -240,11 +251,18 @@ __global__ void __launch_bounds__(NT) k_newton(NewtonDev* nds, int nsolve, int c
             Nn += ((volatile double*)d.red)[2 * q + 1];
         }
         const double diff = sqrt(D), nrm = sqrt(Nn);
-        if (diff < 1e-2 * nrm) scaling = false;
-        if (diff <= d.tol * nrm) {
+        const double rel_step = diff / nrm;
+        // stop at the tolerance; or one step after the relative step fell below
+        // sqrt(tol) (quadratic convergence: this step is at the tolerance); or
+        // when rounding stalls the unscaled iteration (step no longer halves)
+        const bool unscaled = !scaling;
+        if (rel_step <= d.tol || (unscaled && prev_rel <= 1e-10) ||
+            (unscaled && prev_rel < 1e-8 && rel_step > 0.5 * prev_rel)) {
             converged = true;
             break;
         }
+        if (rel_step < 1e-2) scaling = false;
+        prev_rel = rel_step;
         if (!(nrm == nrm)) break;
     }
     if (g == 0 && tid == 0) {
@@ -299,6 +317,7 @@ int ovl_newton_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int cpm, c
                         lat->num_sms * per_sm);
     void* args[] = {(void*)&nd_dev, (void*)&nsolve, (void*)&cpm};
     OVL_CUDA_TRY(lat, cudaLaunchCooperativeKernel((const void*)k_newton, dim3(nsolve * cpm), dim3(NT), args, 0, st));
+    lat->launches++;
     return OVL_OK;
 }
 

@@ -10,6 +10,8 @@
 
 #include "../../include/ovl.h"
 
+#define OVL_PROF_CLASSES 8
+
 // ---------------------------------------------------------------------------
 // Packed spinor order used on the device.
 //
@@ -55,7 +57,29 @@ struct ovl_lattice_s {
     void* ws = nullptr;
     size_t ws_bytes = 0;
     int num_sms = 0;
+    // kernels launched by this handle, and optional per-class event timing
+    long long launches = 0;
+    bool prof = false;
+    double prof_acc[OVL_PROF_CLASSES][3] = {};  // launches, ms, algorithmic bytes
+    struct ProfRec {
+        int cls;
+        cudaEvent_t a, b;
+        double bytes;
+    };
+    std::vector<ProfRec> prof_pending;
+    std::vector<cudaEvent_t> event_pool;
 };
+
+// event-timed region of one kernel class (no-op unless profiling is on)
+struct ProfScope {
+    ovl_lattice lat;
+    int cls;
+    double bytes;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(ovl_lattice l, int c, double by, cudaStream_t st);
+    void end(cudaStream_t st);
+};
+void ovl_prof_flush(ovl_lattice lat);
 
 struct ovl_deflation_s {
     ovl_lattice lat;
@@ -68,6 +92,8 @@ struct ovl_deflation_s {
     float2* L_lo = nullptr;
     double2* T = nullptr;     // Schur: m x m column-major (device); LR: Lambda (m)
     std::vector<double> T_host;  // same data on the host (2*m*m or 2*m doubles)
+    int setup_restarts = 0;      // restarts and operator applications of ovl_deflation_setup
+    int setup_matvecs = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -87,6 +113,7 @@ int ovl_fail(ovl_lattice lat, int code, const char* fmt, ...);
         if (e__ != cudaSuccess)                                                      \
             return ovl_fail((lat), OVL_ECUDA, "kernel launch failed: %s (%s:%d)",    \
                             cudaGetErrorString(e__), __FILE__, __LINE__);            \
+        (lat)->launches++;                                                           \
     } while (0)
 
 // Is p a device (or managed) pointer?

@@ -250,7 +250,7 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         p.nmax = p.m_q + p.k;
         if (p.ldH > OVL_MAXCOL || p.nmax > OVL_NEWTON_MAXN)
             return ovl_fail(lat, OVL_EINVAL, "solve %d: m+k+1=%d exceeds the build limit %d", i, p.ldH, OVL_MAXCOL);
-        if ((size_t)p.k + 1 > N) return ovl_fail(lat, OVL_EINVAL, "solve %d: k=%d exceeds N", i, p.k);
+        if ((size_t)p.k > N) return ovl_fail(lat, OVL_EINVAL, "solve %d: k=%d exceeds N", i, p.k);
         kmax = std::max(kmax, p.k);
         ldmax = std::max(ldmax, p.ldH);
         mdef_max = std::max(mdef_max, p.m_defl);
@@ -396,6 +396,7 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         s.active = 1;
         s.k_used = p.k;
         s.status = 0;
+        s.fin = 1;
         OVL_CUDA_TRY(lat, cudaMemsetAsync(p.H, 0, (size_t)p.ldH * p.ldH * sizeof(double2), st));
         if (p.m_q)
             OVL_CUDA_TRY(lat, cudaMemcpy2DAsync(p.H, p.ldH * sizeof(double2), p.d->T, p.m_q * sizeof(double2),
@@ -453,9 +454,15 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         OVL_CUDA_TRY(lat, cudaMemcpyAsync(p.pu_lo, ul.data(), p.m_defl * sizeof(void*), cudaMemcpyHostToDevice, st));
         OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
     }
-    if (int rc = run_proj(0)) return rc;
-    if (int rc = run_proj(1)) return rc;
-    if (int rc = run_proj(2)) return rc;
+    {
+        double pb = 0.0;
+        for (int i = 0; i < nsolve; i++) pb += (double)N * 16.0 * (2.0 * P[i].m_defl * (P[i].scheme == OVL_DEFL_SCHUR ? 2 : 1) + 6.0);
+        ProfScope ps(lat, 6, pb, st);
+        if (int rc = run_proj(0)) return rc;
+        if (int rc = run_proj(1)) return rc;
+        if (int rc = run_proj(2)) return rc;
+        ps.end(st);
+    }
     // projection coefficients back to the host (m + 1 numbers per solve)
     std::vector<std::vector<double2>> c1(nsolve), c2(nsolve), nrm(nsolve);
     std::vector<double> beta(nsolve);
@@ -510,23 +517,61 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     da.nrhs = nsolve;
     da.kappa = 1.0 / (8.0 + 2.0 * m_w);
     const int links = prec == OVL_PREC_FP64 ? OVL_LINKS_F64 : prec == OVL_PREC_MIXED ? OVL_LINKS_F32 : OVL_LINKS_R12;
+    const double site_bytes = 2.0 * 12 * 16 + 4.0 * (links == OVL_LINKS_F64 ? 144 : links == OVL_LINKS_F32 ? 72 : 48);
+    const double qbytes = df ? 16.0 : 8.0;
     for (int j = 1; j <= kmax; j++) {
-        int pmax = 0;
+        int pmax = 0, nact = 0;
+        double colsum = 0.0;
         for (int i = 0; i < nsolve; i++)
-            if (j <= P[i].k) pmax = std::max(pmax, P[i].m_q + j - 1);
+            if (j <= P[i].k) {
+                pmax = std::max(pmax, P[i].m_q + j - 1);
+                nact++;
+                colsum += P[i].m_q + j - 1;
+            }
         bd.pmax = pmax;
         da.j = j;
+        // algorithmic bytes: stencil 960 B/site (FP64); pass A reads the FP32 high
+        // plane and u, w; pass B reads the full basis, u, w and writes u and q
+        ProfScope p0(lat, 0, nact * (double)lat->V * site_bytes, st);
         if (int rc = ovl_dslash_launch(lat, da, OVL_VEC_F64, links, st)) return rc;
+        p0.end(st);
+        ProfScope p1(lat, 1, colsum * N * 8.0 + nact * 2.0 * N * 16.0, st);
         if (int rc = ovl_gs_dot(lat, bd, j, st)) return rc;
+        p1.end(st);
+        ProfScope p2(lat, 2, 0.0, st);
         if (int rc = ovl_gs_reduce(lat, bd, j, st)) return rc;
+        p2.end(st);
+        ProfScope p3(lat, 3, 0.0, st);
         if (int rc = ovl_gs_small(lat, bd, j, st)) return rc;
+        p3.end(st);
+        ProfScope p4(lat, 4, colsum * N * qbytes + nact * (3.0 * N * 16.0 + N * qbytes), st);
         if (int rc = ovl_gs_update(lat, bd, j, st)) return rc;
+        p4.end(st);
     }
+    // accurate Galerkin correction of the last column (FP64 projection of u)
+    OVL_CUDA_TRY(lat, cudaMemcpyAsync(hs.data(), d_sd, nsolve * sizeof(SolveDev), cudaMemcpyDeviceToHost, st));
+    OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
     {
-        int pmax = 0;
-        for (int i = 0; i < nsolve; i++) pmax = std::max(pmax, P[i].m_q + P[i].k);
+        std::vector<ProjDev> pd(nsolve);
+        int maxcol = 0, pmax = 0;
+        for (int i = 0; i < nsolve; i++) {
+            ProjDev& q = pd[i];
+            q.qhi = P[i].qhi;
+            q.qlo = P[i].qlo;
+            q.x = P[i].u;
+            q.out = P[i].dots;
+            q.coef = nullptr;
+            q.ncol = hs[i].fin ? P[i].m_q + hs[i].k_used : 0;
+            maxcol = std::max(maxcol, q.ncol);
+            pmax = std::max(pmax, q.ncol);
+        }
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_pd, pd.data(), nsolve * sizeof(ProjDev), cudaMemcpyHostToDevice, st));
         bd.pmax = pmax;
-        if (int rc = ovl_gs_final(lat, bd, st)) return rc;
+        double fb = 0.0;
+        for (int i = 0; i < nsolve; i++) fb += (double)pd[i].ncol * N * 16.0 + N * 16.0;
+        ProfScope pf(lat, 6, fb, st);
+        if (int rc = ovl_gs_final(lat, bd, d_pd, maxcol, st)) return rc;
+        pf.end(st);
     }
     OVL_CUDA_TRY(lat, cudaMemcpyAsync(hs.data(), d_sd, nsolve * sizeof(SolveDev), cudaMemcpyDeviceToHost, st));
     OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
@@ -573,8 +618,10 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     if (any_run) {
         int cpm_run = ovl_newton_cpm(lat, nsolve, nmax_run);
         (void)cpm;
+        ProfScope pn(lat, 5, 0.0, st);
         if (int rc = ovl_newton_launch(lat, d_nd, nsolve, cpm_run, st)) return rc;
         if (int rc = ovl_fmatvec_launch(lat, d_nd, nsolve, nmax_run, st)) return rc;
+        pn.end(st);
     }
     std::vector<int> nstat(nsolve, 0), nit(nsolve, 0);
     for (int i = 0; i < nsolve; i++) {
@@ -624,7 +671,11 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         gmax = std::max(gmax, gd[i].ncol);
     }
     OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_gd, gd.data(), nsolve * sizeof(GemvDev), cudaMemcpyHostToDevice, st));
+    double gb = 0.0;
+    for (int i = 0; i < nsolve; i++) gb += (double)gd[i].ncol * N * 16.0 + N * 16.0;
+    ProfScope pg(lat, 7, gb, st);
     if (int rc = ovl_gemv_df(lat, d_gd, nsolve, gmax, st)) return rc;
+    pg.end(st);
     // ---- outputs ----
     bool ydev = ovl_is_device_ptr(y);
     for (int i = 0; i < nsolve; i++) {
@@ -649,18 +700,14 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             info[i].beta_k = bk;
         }
     }
+    ovl_prof_flush(lat);
     if (first_bad) return ovl_fail(lat, first_bad, "ovl_sign_apply: a solve failed (first status %d)", first_bad);
     return OVL_OK;
 }
 
-extern "C" int ovl_deflation_setup(ovl_lattice lat, double mu, double m_w, int scheme, int m, double tol,
-                                   int max_restarts, ovl_deflation* out) {
-    (void)mu;
-    (void)m_w;
-    (void)scheme;
-    (void)m;
-    (void)tol;
-    (void)max_restarts;
-    (void)out;
-    return ovl_fail(lat, OVL_ENOTSUP, "ovl_deflation_setup: eigensolver not built yet");
+extern "C" int ovl_deflation_stats(ovl_deflation d, int* restarts, int* matvecs) {
+    if (!d) return ovl_fail(nullptr, OVL_EINVAL, "ovl_deflation_stats: null handle");
+    if (restarts) *restarts = d->setup_restarts;
+    if (matvecs) *matvecs = d->setup_matvecs;
+    return OVL_OK;
 }

@@ -52,8 +52,11 @@ _SIGS = {
                                       C.POINTER(_P)]),
     "ovl_get_deflation": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), _P, _P, _P]),
     "ovl_destroy_deflation": (C.c_int, [_P]),
+    "ovl_deflation_stats": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "ovl_sign_apply": (C.c_int, [_P, C.c_int, C.POINTER(ovl_sign_params), C.POINTER(_P), _P, _P,
                                  C.POINTER(ovl_sign_info)]),
+    "ovl_launch_count": (C.c_int, [_P, C.POINTER(C.c_longlong)]),
+    "ovl_profile": (C.c_int, [_P, C.c_int, _P]),
     "ovl_last_error": (C.c_char_p, [_P]),
     "ovl_version": (C.c_char_p, []),
 }
@@ -162,6 +165,12 @@ def ovl_get_deflation(d, S_or_R=None, T=None, L=None, h=None):
     return sch.value, m.value
 
 
+def ovl_deflation_stats(d):
+    r, m = C.c_int(), C.c_int()
+    _check(lib().ovl_deflation_stats(d, C.byref(r), C.byref(m)))
+    return r.value, m.value
+
+
 def ovl_destroy_deflation(d):
     _check(lib().ovl_destroy_deflation(d))
 
@@ -189,6 +198,25 @@ def ovl_sign_apply(h, params, defl, b, y, info=True):
         err.infos = infos
         raise err
     return infos
+
+
+def ovl_launch_count(h):
+    n = C.c_longlong()
+    _check(lib().ovl_launch_count(h, C.byref(n)), h)
+    return n.value
+
+
+PROF_CLASSES = ["stencil", "gs_pass_a", "gs_reduce", "gs_small", "gs_pass_b", "newton", "projection",
+                "recombination"]
+
+
+def ovl_profile(h, enable):
+    """Start (enable=1, clears) or stop (0) per-class timing; returns the
+    per-class {launches, ms, bytes} collected so far."""
+    buf = (C.c_double * (3 * len(PROF_CLASSES)))()
+    _check(lib().ovl_profile(h, int(enable), C.cast(buf, _P)), h)
+    return {n: dict(launches=int(buf[3 * i]), ms=buf[3 * i + 1], bytes=buf[3 * i + 2])
+            for i, n in enumerate(PROF_CLASSES)}
 
 
 def ovl_last_error(h=None):

@@ -113,3 +113,12 @@ def ones_source(dims) -> np.ndarray:
     """x = (1, 1, ..., 1), the source of the paper's convergence figure."""
     shp = lattice_shape(dims) + (4, 3)
     return np.ones(shp, dtype=np.complex128)
+
+
+def probe_vectors(n: int, count: int, seed: int = 12345) -> np.ndarray:
+    """``count`` complex Gaussian probe vectors of length n (re, im ~ N(0,1)),
+    used to sketch a long result vector by a few inner products."""
+    rng = np.random.default_rng(seed)
+    re = rng.standard_normal((count, n))
+    im = rng.standard_normal((count, n))
+    return re + 1j * im
