@@ -103,6 +103,21 @@ int ovl_set_links(ovl_lattice lat, const double* U);
 int ovl_apply_Hw(ovl_lattice lat, double mu, double m_w, const double* in, double* out,
                  int nrhs, int links);
 
+/* ovl_apply_Hw without any device allocation, for callers that cannot let
+ * the library allocate (all free HBM handed to the caller's own pool, code
+ * that must avoid the implicit synchronisation of cudaMalloc/cudaFree, or a
+ * runtime that accounts for every device byte up front). The paper has no
+ * counterpart: this is an allocation-free variant of ovl_apply_Hw.
+ * in/out: device pointers only (canonical layout, nrhs vectors); results
+ * equal ovl_apply_Hw's. Staging uses one fixed 32 MiB device array that every
+ * GPU loading the library holds until exit; 2 * nrhs packed spinors plus 24
+ * bytes per right-hand side must fit (OVL_EINVAL otherwise). The first call
+ * on a device looks up that array's address (cudaGetSymbolAddress) and should
+ * come before any stream capture. Calls share the array: calls that overlap
+ * on the GPU race. Never calls cudaMalloc or cudaFree. */
+int ovl_apply_Hw_noalloc(ovl_lattice lat, double mu, double m_w, const double* in, double* out,
+                         int nrhs, int links);
+
 /* Stencil on packed spinors (the library's internal site order), for timing
  * the stencil alone. in/out: device pointers, nrhs vectors of 12*V complex in
  * format fmt (OVL_VEC_*); mu: nrhs chemical potentials (host array).

@@ -44,6 +44,7 @@ _SIGS = {
     "ovl_destroy_lattice": (C.c_int, [_P]),
     "ovl_set_links": (C.c_int, [_P, _P]),
     "ovl_apply_Hw": (C.c_int, [_P, C.c_double, C.c_double, _P, _P, C.c_int, C.c_int]),
+    "ovl_apply_Hw_noalloc": (C.c_int, [_P, C.c_double, C.c_double, _P, _P, C.c_int, C.c_int]),
     "ovl_apply_Hw_packed": (C.c_int, [_P, _P, C.c_double, _P, _P, C.c_int, C.c_int, C.c_int]),
     "ovl_pack_spinor": (C.c_int, [_P, _P, _P, C.c_int, C.c_int]),
     "ovl_unpack_spinor": (C.c_int, [_P, _P, _P, C.c_int, C.c_int]),
@@ -127,6 +128,12 @@ def ovl_set_links(h, U):
 
 def ovl_apply_Hw(h, mu, m_w, x, out, nrhs=1, links=OVL_LINKS_F64):
     _check(lib().ovl_apply_Hw(h, float(mu), float(m_w), _ptr(x), _ptr(out), int(nrhs), int(links)), h)
+    return out
+
+
+def ovl_apply_Hw_noalloc(h, mu, m_w, x, out, nrhs=1, links=OVL_LINKS_F64):
+    """ovl_apply_Hw without device allocation (device tensors only)."""
+    _check(lib().ovl_apply_Hw_noalloc(h, float(mu), float(m_w), _ptr(x), _ptr(out), int(nrhs), int(links)), h)
     return out
 
 
