@@ -72,6 +72,7 @@ typedef struct {
     int    prec;        /* OVL_PREC_* */
     int    newton_max_iter;  /* <= 0: default 100 */
     double newton_tol;       /* <= 0: default 1e-13 (relative Frobenius step) */
+    int    newton_fp64;      /* 0: double-float Gauss-Jordan (default); 1: FP64 Gauss-Jordan */
 } ovl_sign_params;
 
 typedef struct {

@@ -100,3 +100,65 @@ __device__ __forceinline__ void dfacc_add(dfacc& a, const dfacc& b) {
 __device__ __forceinline__ double2 dfacc_value(const dfacc& a) {
     return make_double2((double)a.s.x + (double)a.t.x, (double)a.s.y + (double)a.t.y);
 }
+
+// ---- complex df values (Newton sign): hi + lo, each a complex FP32 -------
+__device__ __forceinline__ dfc dfc_make(float2 hi, float2 lo) {
+    dfc r;
+    r.hi = hi;
+    r.lo = lo;
+    return r;
+}
+__device__ __forceinline__ float4 dfc_pack(const dfc& a) { return make_float4(a.hi.x, a.hi.y, a.lo.x, a.lo.y); }
+__device__ __forceinline__ dfc dfc_unpack(float4 v) { return dfc_make(make_float2(v.x, v.y), make_float2(v.z, v.w)); }
+// renormalise a real df pair (s, t) so that |t| <= ulp(s)/2
+__device__ __forceinline__ void df_norm(float& s, float& t) {
+    float a, b;
+    fast_two_sum(s, t, a, b);
+    s = a;
+    t = b;
+}
+// c - a * b  (all complex df), error about 2^-46 relative to |a||b| + |c|
+__device__ __forceinline__ dfc dfc_fms(const dfc& c, const dfc& a, const dfc& b) {
+    float p, e, s, err;
+    dfc r;
+    // real: c.re - (a.re b.re - a.im b.im)
+    float sr = c.hi.x, tr = c.lo.x;
+    two_prod(a.hi.x, b.hi.x, p, e);
+    two_sum(sr, -p, s, err);
+    sr = s;
+    tr = __fadd_rn(tr, __fsub_rn(err, e));
+    two_prod(a.hi.y, b.hi.y, p, e);
+    two_sum(sr, p, s, err);
+    sr = s;
+    tr = __fadd_rn(tr, __fadd_rn(err, e));
+    tr = fmaf(-a.hi.x, b.lo.x, tr);
+    tr = fmaf(-a.lo.x, b.hi.x, tr);
+    tr = fmaf(a.hi.y, b.lo.y, tr);
+    tr = fmaf(a.lo.y, b.hi.y, tr);
+    df_norm(sr, tr);
+    // imag: c.im - (a.re b.im + a.im b.re)
+    float si = c.hi.y, ti = c.lo.y;
+    two_prod(a.hi.x, b.hi.y, p, e);
+    two_sum(si, -p, s, err);
+    si = s;
+    ti = __fadd_rn(ti, __fsub_rn(err, e));
+    two_prod(a.hi.y, b.hi.x, p, e);
+    two_sum(si, -p, s, err);
+    si = s;
+    ti = __fadd_rn(ti, __fsub_rn(err, e));
+    ti = fmaf(-a.hi.x, b.lo.y, ti);
+    ti = fmaf(-a.lo.x, b.hi.y, ti);
+    ti = fmaf(-a.hi.y, b.lo.x, ti);
+    ti = fmaf(-a.lo.y, b.hi.x, ti);
+    df_norm(si, ti);
+    r.hi = make_float2(sr, si);
+    r.lo = make_float2(tr, ti);
+    return r;
+}
+__device__ __forceinline__ dfc dfc_zero() { return dfc_make(make_float2(0.f, 0.f), make_float2(0.f, 0.f)); }
+__device__ __forceinline__ dfc dfc_mul(const dfc& a, const dfc& b) { return dfc_fms(dfc_zero(), dfc_make(make_float2(-a.hi.x, -a.hi.y), make_float2(-a.lo.x, -a.lo.y)), b); }
+// s * a + t * b for real FP64 scalars s, t (via FP64 on the two parts: used once per element per iteration)
+__device__ __forceinline__ dfc dfc_axpby(double s, const dfc& a, double t, const dfc& b) {
+    double2 x = dfc_to(a), y = dfc_to(b);
+    return dfc_from(make_double2(s * x.x + t * y.x, s * x.y + t * y.y));
+}

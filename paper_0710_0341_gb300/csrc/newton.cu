@@ -281,9 +281,16 @@ __global__ void __launch_bounds__(256) k_fmatvec(NewtonDev* nds, int nsolve) {
     const int i = blockIdx.x * 8 + warp;
     if (i >= n) return;
     const double2* row = d.X + (size_t)i * n;
+    const float4* rowf = (const float4*)row;
     double2 acc = make_double2(0.0, 0.0);
     for (int l = lane; l < n; l += 32) {
-        double2 a = row[l], b = d.cvec[l];
+        double2 a, b = d.cvec[l];
+        if (d.df) {
+            float4 v = rowf[l];
+            a = make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+        } else {
+            a = row[l];
+        }
         acc.x += a.x * b.x - a.y * b.y;
         acc.y += a.x * b.y + a.y * b.x;
     }
@@ -325,5 +332,262 @@ int ovl_fmatvec_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int nmax,
     dim3 grid((nmax + 7) / 8, nsolve);
     k_fmatvec<<<grid, 256, 0, st>>>(nd_dev, nsolve);
     OVL_LAUNCH_CHECK(lat);
+    return OVL_OK;
+}
+
+// ===========================================================================
+// Double-float variant. GB300 issues FP64 at ~2 FMA/clock/SM and FP32 at 128,
+// so the elimination runs in double-float (48-bit) arithmetic on the FP32
+// pipes; only per-pivot scalars (reciprocal, log |pivot|) use FP64. Each CTA
+// of a group keeps its rows of the work matrix in shared memory when they fit.
+// Before every barrier each CTA publishes its best pivot candidate row to
+// global memory, so the winning row is read by all CTAs right after the one
+// barrier per pivot; the owner overwrites its copy with the scaled row.
+// ===========================================================================
+#include "df.cuh"
+
+namespace {
+
+template <bool SMEM>
+__global__ void __launch_bounds__(NT, 1) k_newton_df(NewtonDev* nds, int nsolve, int cpm) {
+    extern __shared__ float4 dsm[];
+    const int s = blockIdx.x / cpm;
+    const int g = blockIdx.x % cpm;
+    if (s >= nsolve) return;
+    NewtonDev& d = nds[s];
+    if (!d.run) return;
+    const int n = d.n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nr = (n - g + cpm - 1) / cpm;  // own rows: i = g + cpm * r
+    float4* X = (float4*)d.X;
+    float4* R = SMEM ? dsm : d.Wg + (size_t)g * (size_t)((n + cpm - 1) / cpm) * n;
+    float4* prow = SMEM ? dsm + (size_t)nr * n : (float4*)(dsm);
+    float4* fcol = prow + n;                          // nr values of column k
+    int* piv = (int*)(fcol + ((nr + 1) & ~1));
+    int* pinv = piv + n;
+    unsigned char* used = (unsigned char*)(pinv + n);
+    __shared__ float s_red[NT / 32];
+    __shared__ int s_idx[NT / 32];
+    __shared__ float4 s_inv;
+    __shared__ double s_logdet, s_c;
+    __shared__ float s_nrm[2][NT / 32];
+    unsigned gen = 0;
+    // X_0 = H (column-major FP64 input)
+    for (int r = 0; r < nr; r++) {
+        int i = g + cpm * r;
+        for (int l = tid; l < n; l += NT) X[(size_t)i * n + l] = dfc_pack(dfc_from(d.H[i + (size_t)l * d.ldH]));
+    }
+    bool scaling = true, converged = false;
+    double prev_rel = 1e300;
+    int iter = 0;
+    if (!group_sync(d, gen, cpm)) return;
+    while (iter < d.max_iter) {
+        iter++;
+        for (int r = 0; r < nr; r++) {
+            int i = g + cpm * r;
+            for (int l = tid; l < n; l += NT) R[(size_t)r * n + l] = __ldcg(X + (size_t)i * n + l);
+        }
+        for (int i = tid; i < n; i += NT) used[i] = 0;
+        if (tid == 0) s_logdet = 0.0;
+        __syncthreads();
+        int bad = 0;
+        for (int k = 0; k < n; k++) {
+            // best unused own row for column k (|hi|^2), published with its data
+            float best = -1.f;
+            int br = -1;
+            for (int r = tid; r < nr; r += NT) {
+                int i = g + cpm * r;
+                if (used[i]) continue;
+                float4 v = R[(size_t)r * n + k];
+                float a = v.x * v.x + v.y * v.y;
+                if (a > best) {
+                    best = a;
+                    br = r;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                float ov = __shfl_xor_sync(0xffffffffu, best, o);
+                int oi = __shfl_xor_sync(0xffffffffu, br, o);
+                if (ov > best || (ov == best && oi >= 0 && (br < 0 || oi < br))) {
+                    best = ov;
+                    br = oi;
+                }
+            }
+            if (lane == 0) {
+                s_red[warp] = best;
+                s_idx[warp] = br;
+            }
+            __syncthreads();
+            best = s_red[0];
+            br = s_idx[0];
+            for (int w = 1; w < NT / 32; w++)
+                if (s_red[w] > best || (s_red[w] == best && s_idx[w] >= 0 && (br < 0 || s_idx[w] < br))) {
+                    best = s_red[w];
+                    br = s_idx[w];
+                }
+            const int slot = (k & 1) * cpm + g;
+            if (br >= 0)
+                for (int l = tid; l < n; l += NT) d.crow[(size_t)slot * n + l] = R[(size_t)br * n + l];
+            if (tid == 0) {
+                d.cand_val[slot] = br >= 0 ? (double)best : -1.0;
+                d.cand_row[slot] = br >= 0 ? g + cpm * br : 0x7fffffff;
+            }
+            if (!group_sync(d, gen, cpm)) return;
+            // winner (same choice in every CTA: largest |pivot|, then smallest row)
+            double bv = -1.0;
+            int pr = 0x7fffffff, q = -1;
+            for (int c = 0; c < cpm; c++) {
+                double v = ((volatile double*)d.cand_val)[(k & 1) * cpm + c];
+                int rw = ((volatile int*)d.cand_row)[(k & 1) * cpm + c];
+                if (v > bv || (v == bv && rw < pr)) {
+                    bv = v;
+                    pr = rw;
+                    q = c;
+                }
+            }
+            if (!(bv > 0.0) || q < 0) {
+                bad = 1;
+                break;
+            }
+            const float4* pw = d.crow + (size_t)((k & 1) * cpm + q) * n;
+            if (tid == 0) {
+                double2 pv = dfc_to(dfc_unpack(__ldcg(pw + k)));
+                double2 inv = cinv(pv);
+                s_inv = dfc_pack(dfc_from(inv));
+                s_logdet += 0.5 * log(cabs2(pv));
+                used[pr] = 1;
+                piv[k] = pr;
+            }
+            // f values of own rows before they change
+            for (int r = tid; r < nr; r += NT) fcol[r] = R[(size_t)r * n + k];
+            __syncthreads();
+            const dfc inv = dfc_unpack(s_inv);
+            for (int l = tid; l < n; l += NT)
+                prow[l] = l == k ? s_inv : dfc_pack(dfc_mul(dfc_unpack(__ldcg(pw + l)), inv));
+            __syncthreads();
+            const int rp = (pr % cpm == g) ? (pr - g) / cpm : -1;  // own index of the pivot row
+            for (int r = 0; r < nr; r++) {
+                float4* row = R + (size_t)r * n;
+                if (r == rp) {
+                    for (int l = tid; l < n; l += NT) row[l] = prow[l];
+                    continue;
+                }
+                const dfc f = dfc_unpack(fcol[r]);
+                if (f.hi.x == 0.f && f.hi.y == 0.f && f.lo.x == 0.f && f.lo.y == 0.f) continue;
+                for (int l = tid; l < n; l += NT) {
+                    dfc pl = dfc_unpack(prow[l]);
+                    if (l == k)
+                        row[l] = dfc_pack(dfc_fms(dfc_zero(), f, pl));
+                    else
+                        row[l] = dfc_pack(dfc_fms(dfc_unpack(row[l]), f, pl));
+                }
+            }
+            __syncthreads();
+        }
+        if (bad) {
+            if (tid == 0 && g == 0) atomicExch(d.status, OVL_ENOCONV);
+            return;
+        }
+        for (int k = tid; k < n; k += NT) pinv[piv[k]] = k;
+        if (tid == 0) s_c = scaling ? exp(-s_logdet / n) : 1.0;
+        __syncthreads();
+        // inverse: Xinv[pinv(q)][piv[j]] = St[q][j] for the own stored rows q;
+        // X_new row pinv(q) = (c X + Xinv / c) / 2, written by this CTA only
+        const double c = s_c, ic = 1.0 / c;
+        float dsum = 0.f, nsum = 0.f;
+        for (int r = 0; r < nr; r++) {
+            const int qrow = g + cpm * r;
+            const int i = pinv[qrow];
+            float4* xr = X + (size_t)i * n;
+            for (int j = tid; j < n; j += NT) {
+                const int l = piv[j];
+                dfc xo = dfc_unpack(__ldcg(xr + l));  // rows of X move between CTAs
+                dfc a = dfc_unpack(R[(size_t)r * n + j]);
+                dfc xn = dfc_axpby(0.5 * c, xo, 0.5 * ic, a);
+                float dr = (xn.hi.x - xo.hi.x) + (xn.lo.x - xo.lo.x);
+                float di = (xn.hi.y - xo.hi.y) + (xn.lo.y - xo.lo.y);
+                dsum += dr * dr + di * di;
+                nsum += xn.hi.x * xn.hi.x + xn.hi.y * xn.hi.y;
+                xr[l] = dfc_pack(xn);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+            nsum += __shfl_xor_sync(0xffffffffu, nsum, o);
+        }
+        if (lane == 0) {
+            s_nrm[0][warp] = dsum;
+            s_nrm[1][warp] = nsum;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0.0, b = 0.0;
+            for (int w = 0; w < NT / 32; w++) {
+                a += s_nrm[0][w];
+                b += s_nrm[1][w];
+            }
+            d.red[2 * g] = a;
+            d.red[2 * g + 1] = b;
+        }
+        if (!group_sync(d, gen, cpm)) return;
+        double D = 0.0, Nn = 0.0;
+        for (int c2 = 0; c2 < cpm; c2++) {
+            D += ((volatile double*)d.red)[2 * c2];
+            Nn += ((volatile double*)d.red)[2 * c2 + 1];
+        }
+        const double rel_step = sqrt(D) / sqrt(Nn);
+        const bool unscaled = !scaling;
+        if (rel_step <= d.tol || (unscaled && prev_rel <= 1e-10) ||
+            (unscaled && prev_rel < 1e-8 && rel_step > 0.5 * prev_rel)) {
+            converged = true;
+            break;
+        }
+        if (rel_step < 1e-2) scaling = false;
+        prev_rel = rel_step;
+        if (!(Nn == Nn)) break;
+    }
+    if (g == 0 && tid == 0) {
+        *d.iters = iter;
+        if (!converged) atomicCAS(d.status, 0, OVL_ENOCONV);
+    }
+}
+
+size_t df_smem_bytes(int n, int nr, bool rows) {
+    size_t b = 0;
+    if (rows) b += (size_t)nr * n * sizeof(float4);
+    b += (size_t)n * sizeof(float4);                  // prow
+    b += (size_t)((nr + 1) & ~1) * sizeof(float4);    // fcol
+    b += 2 * (size_t)n * sizeof(int) + (size_t)n + 64;  // piv, pinv, used
+    return (b + 15) & ~(size_t)15;
+}
+
+}  // namespace
+
+int ovl_newton_df_plan(ovl_lattice lat, int nsolve, int nmax, int* cpm_out, int* smem_rows) {
+    int cpm = lat->num_sms / (nsolve > 0 ? nsolve : 1);
+    int want = (nmax + 3) / 4;  // at least 4 rows per CTA
+    if (cpm > want) cpm = want;
+    if (cpm > 64) cpm = 64;
+    if (cpm < 1) cpm = 1;
+    int nr = (nmax + cpm - 1) / cpm;
+    *smem_rows = df_smem_bytes(nmax, nr, true) <= 200 * 1024 ? 1 : 0;
+    *cpm_out = cpm;
+    return OVL_OK;
+}
+
+int ovl_newton_df_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int nmax, int cpm, int smem_rows,
+                         cudaStream_t st) {
+    int nr = (nmax + cpm - 1) / cpm;
+    size_t smem = df_smem_bytes(nmax, nr, smem_rows != 0);
+    const void* fn = smem_rows ? (const void*)k_newton_df<true> : (const void*)k_newton_df<false>;
+    OVL_CUDA_TRY(lat, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessorWithFlags(&per_sm, fn, NT, smem, cudaOccupancyDefault);
+    if (per_sm < 1 || (long)nsolve * cpm > (long)lat->num_sms * per_sm)
+        return ovl_fail(lat, OVL_EINVAL, "Newton batch of %d x %d blocks exceeds co-residency (%d per SM)", nsolve,
+                        cpm, per_sm);
+    void* args[] = {(void*)&nd_dev, (void*)&nsolve, (void*)&cpm};
+    OVL_CUDA_TRY(lat, cudaLaunchCooperativeKernel(fn, dim3(nsolve * cpm), dim3(NT), args, smem, st));
+    lat->launches++;
     return OVL_OK;
 }

@@ -21,8 +21,15 @@ struct NewtonDev {
     int* iters;
     const double2* cvec;  // coefficient vector (n) for F c
     double2* gout;        // F c (n)
+    int df;               // 1: X holds double-float values (float4 hi.re, hi.im, lo.re, lo.im)
+    float4* crow;         // df kernel: published candidate rows, 2 x CTAs x n
+    float4* Wg;           // df kernel: work rows in global memory when they do not fit in shared memory
 };
 
 int ovl_newton_cpm(ovl_lattice lat, int nsolve, int nmax);
 int ovl_newton_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int cpm, cudaStream_t st);
+// double-float Gauss-Jordan Newton (rows in shared memory when they fit)
+int ovl_newton_df_plan(ovl_lattice lat, int nsolve, int nmax, int* cpm, int* smem_rows);
+int ovl_newton_df_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int nmax, int cpm, int smem_rows,
+                         cudaStream_t st);
 int ovl_fmatvec_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int nmax, cudaStream_t st);

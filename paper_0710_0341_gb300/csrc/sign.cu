@@ -200,6 +200,7 @@ struct SolvePlan {
     const float2** qhi = nullptr;
     const float2** qlo = nullptr;
     double2 *X = nullptr, *W = nullptr;
+    float4* crow = nullptr;
     double *cand_val = nullptr, *red = nullptr;
     int* cand_row = nullptr;
     unsigned* bar = nullptr;
@@ -284,7 +285,8 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             t(p.qhi, ld);
             t(p.qlo, ld);
             t(p.X, nm * nm);
-            t(p.W, nm * nm);
+            t(p.W, nm * nm + 64 * nm);
+            t(p.crow, 2 * 64 * nm);
             t(p.cand_val, 128);
             t(p.cand_row, 128);
             t(p.red, 128);
@@ -599,6 +601,9 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         q.iters = p.iters;
         q.cvec = p.cvec;
         q.gout = p.gcomb;
+        q.df = params[0].newton_fp64 ? 0 : 1;
+        q.crow = p.crow;
+        q.Wg = (float4*)p.W;
         if (q.run) {
             any_run = 1;
             nmax_run = std::max(nmax_run, n);
@@ -619,7 +624,13 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         int cpm_run = ovl_newton_cpm(lat, nsolve, nmax_run);
         (void)cpm;
         ProfScope pn(lat, 5, 0.0, st);
-        if (int rc = ovl_newton_launch(lat, d_nd, nsolve, cpm_run, st)) return rc;
+        if (params[0].newton_fp64) {
+            if (int rc = ovl_newton_launch(lat, d_nd, nsolve, cpm_run, st)) return rc;
+        } else {
+            int cpm_df = 1, smem_rows = 0;
+            ovl_newton_df_plan(lat, nsolve, nmax_run, &cpm_df, &smem_rows);
+            if (int rc = ovl_newton_df_launch(lat, d_nd, nsolve, nmax_run, cpm_df, smem_rows, st)) return rc;
+        }
         if (int rc = ovl_fmatvec_launch(lat, d_nd, nsolve, nmax_run, st)) return rc;
         pn.end(st);
     }

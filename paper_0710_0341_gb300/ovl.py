@@ -29,7 +29,7 @@ class OvlError(RuntimeError):
 
 class ovl_sign_params(C.Structure):
     _fields_ = [("mu", C.c_double), ("m_w", C.c_double), ("k", C.c_int), ("prec", C.c_int),
-                ("newton_max_iter", C.c_int), ("newton_tol", C.c_double)]
+                ("newton_max_iter", C.c_int), ("newton_tol", C.c_double), ("newton_fp64", C.c_int)]
 
 
 class ovl_sign_info(C.Structure):
@@ -194,6 +194,7 @@ def ovl_sign_apply(h, params, defl, b, y, info=True):
         P[i].prec = int(p.get("prec", OVL_PREC_FP64))
         P[i].newton_max_iter = int(p.get("newton_max_iter", 0))
         P[i].newton_tol = float(p.get("newton_tol", 0.0))
+        P[i].newton_fp64 = int(p.get("newton_fp64", 0))
     D = (_P * n)(*[(d.value if isinstance(d, _P) else d) if d is not None else None for d in (defl or [None] * n)])
     I = (ovl_sign_info * n)()
     rc = lib().ovl_sign_apply(h, n, P, D, _ptr(b), _ptr(y), I)

@@ -221,3 +221,28 @@ def test_sign_argument_errors():
         assert e.value.code == ovl.OVL_EINVAL
     finally:
         ovl.ovl_destroy_lattice(h)
+
+
+def test_newton_double_float_matches_fp64_newton():
+    """The double-float Gauss-Jordan Newton (default) and the FP64 one give the
+    same sign of the projected matrix to well inside the 1e-10 parity bar."""
+    need_gpu()
+    mu, m_w = 0.3, -1.0
+    U, A = _setup(DIMS, 0.5, mu, m_w)
+    S, T, lam, R, L = _schur(A, DIMS, 12)
+    b = synth.gaussian_source(DIMS, 1)
+    h = lattice(DIMS, U)
+    try:
+        ds = _defl_schur(h, mu, m_w, S, T, DIMS)
+        dl = _defl_lr(h, mu, m_w, lam, R, L, DIMS)
+        bb = np.stack([b, b, b])
+        y_df = np.zeros_like(bb)
+        y_64 = np.zeros_like(bb)
+        p = dict(mu=mu, m_w=m_w, k=60)
+        i1 = ovl.ovl_sign_apply(h, [p] * 3, [ds, dl, None], bb, y_df)
+        i2 = ovl.ovl_sign_apply(h, [dict(p, newton_fp64=1)] * 3, [ds, dl, None], bb, y_64)
+        for i in range(3):
+            assert rel(y_df[i], y_64[i]) < 1e-11, (i, rel(y_df[i], y_64[i]))
+            assert i1[i]["newton_iters"] > 0 and i2[i]["newton_iters"] > 0
+    finally:
+        ovl.ovl_destroy_lattice(h)
