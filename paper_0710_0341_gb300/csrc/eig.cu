@@ -265,6 +265,9 @@ class Solver {
             memset(&s, 0, sizeof s);
             s.qhi = qhi;
             s.qlo = qlo;
+            s.vhi = cur_hi;
+            s.vlo = cur_lo;
+            s.nptr = 0;
             s.u = u;
             s.w = w;
             s.H = H;

@@ -15,6 +15,8 @@
 // pass-B arithmetic for whatever coefficients are used, so the inner products
 // of pass A only need FP32 products (they steer orthogonality), while pass B
 // accumulates in double-float (48 bits) against the stored hi+lo basis.
+#include <algorithm>
+
 #include "df.cuh"
 #include "krylov.cuh"
 
@@ -45,73 +47,90 @@ __device__ __forceinline__ bool solve_in_step(const SolveDev& d, int j) {
 
 // ---------------------------------------------------------------------------
 // pass A: a = Q_p^dag u, b = Q_p^dag w and the scalars |u|^2, u^dag w, |w|^2
+//
+// A CTA takes a block of DOT_RB rows (u and w staged in shared memory as
+// FP32) and a group of columns (c = cg + CG * (warp + 8 i)); a warp streams one
+// column at a time, each lane reading 16 float4 (32 rows) of it, and reduces
+// across lanes once per column and row block. Row blocks are visited in a
+// grid-stride loop; each CTA keeps FP64 sums in shared memory and writes one
+// partial per column. grid = (row-block slots G, solves, column groups CG).
 // ---------------------------------------------------------------------------
+constexpr int DOTB_RB = 1024;               // rows per block
+constexpr int DOTB_FL = DOTB_RB / 64;       // float4 loads per lane per column (16)
+
 __global__ void __launch_bounds__(DOT_THREADS) k_gs_dot(BatchDev B, int j) {
     const int s = blockIdx.y;
     const SolveDev& d = B.sd[s];
     if (!solve_in_step(d, j)) return;
     const int p = solve_p(d, j);
     const size_t N = B.N;
+    const int CG = gridDim.z, cg = blockIdx.z;
     __shared__ double2 acc[2 * OVL_MAXCOL + 3];
+    __shared__ const float2* s_col[OVL_MAXPTR];
+    __shared__ float4 s_uw[DOTB_RB];  // (u.re, u.im, w.re, w.im) per row
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nptr = d.nptr;
     for (int o = tid; o < 2 * p + 3; o += DOT_THREADS) acc[o] = make_double2(0.0, 0.0);
-    __syncthreads();
+    for (int c = tid; c < nptr && c < p; c += DOT_THREADS) s_col[c] = d.qhi[c];
     const double2* __restrict__ u = d.u;
     const double2* __restrict__ w = d.w;
-    for (size_t base = (size_t)blockIdx.x * DOT_RB; base < N; base += (size_t)gridDim.x * DOT_RB) {
-        float2 uf[DOT_RPL], wf[DOT_RPL];
-#pragma unroll
-        for (int i = 0; i < DOT_RPL / 2; i++) {
-            size_t r = base + 64 * i + 2 * lane;
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                if (r + h < N) {
-                    double2 a = u[r + h], b = w[r + h];
-                    uf[2 * i + h] = make_float2((float)a.x, (float)a.y);
-                    wf[2 * i + h] = make_float2((float)b.x, (float)b.y);
-                } else {
-                    uf[2 * i + h] = make_float2(0.f, 0.f);
-                    wf[2 * i + h] = make_float2(0.f, 0.f);
-                }
+    for (size_t base = (size_t)blockIdx.x * DOTB_RB; base < N; base += (size_t)gridDim.x * DOTB_RB) {
+        __syncthreads();  // s_uw reuse
+        float guu = 0.f, guwr = 0.f, guwi = 0.f, gww = 0.f;
+        for (int rr = tid; rr < DOTB_RB; rr += DOT_THREADS) {
+            size_t r = base + rr;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < N) {
+                double2 a = u[r], b = w[r];
+                v = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
             }
+            s_uw[rr] = v;
+            guu = fmaf(v.x, v.x, fmaf(v.y, v.y, guu));
+            gww = fmaf(v.z, v.z, fmaf(v.w, v.w, gww));
+            guwr = fmaf(v.x, v.z, fmaf(v.y, v.w, guwr));
+            guwi = fmaf(v.x, v.w, fmaf(-v.y, v.z, guwi));
         }
-        if (warp == 0) {
-            float guu = 0.f, guwr = 0.f, guwi = 0.f, gww = 0.f;
-#pragma unroll
-            for (int i = 0; i < DOT_RPL; i++) {
-                guu = fmaf(uf[i].x, uf[i].x, fmaf(uf[i].y, uf[i].y, guu));
-                gww = fmaf(wf[i].x, wf[i].x, fmaf(wf[i].y, wf[i].y, gww));
-                guwr = fmaf(uf[i].x, wf[i].x, fmaf(uf[i].y, wf[i].y, guwr));
-                guwi = fmaf(uf[i].x, wf[i].y, fmaf(-uf[i].y, wf[i].x, guwi));
-            }
+        if (cg == 0) {
             guu = warp_sum(guu);
             gww = warp_sum(gww);
             guwr = warp_sum(guwr);
             guwi = warp_sum(guwi);
             if (lane == 0) {
-                acc[2 * p].x += guu;
-                acc[2 * p + 1].x += guwr;
-                acc[2 * p + 1].y += guwi;
-                acc[2 * p + 2].x += gww;
+                atomicAdd(&acc[2 * p].x, (double)guu);
+                atomicAdd(&acc[2 * p + 1].x, (double)guwr);
+                atomicAdd(&acc[2 * p + 1].y, (double)guwi);
+                atomicAdd(&acc[2 * p + 2].x, (double)gww);
             }
         }
-        const bool full = base + DOT_RB <= N;
-        for (int c = warp; c < p; c += DOT_THREADS / 32) {
-            const float4* __restrict__ q = (const float4*)d.qhi[c];
+        __syncthreads();
+        const bool full = base + DOTB_RB <= N;
+        for (int c = cg + CG * warp; c < p; c += CG * (DOT_THREADS / 32)) {
+            const float4* __restrict__ q =
+                (const float4*)(c < nptr ? s_col[c] : d.vhi + (size_t)(c - nptr) * N) + (base >> 1);
             float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
 #pragma unroll
-            for (int i = 0; i < DOT_RPL / 2; i++) {
-                size_t r = base + 64 * i + 2 * lane;  // even, pairs (r, r+1)
-                float4 qq = (full || r < N) ? __ldg(q + (r >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
-                // conj(q) * u
-                ar = fmaf(qq.x, uf[2 * i].x, fmaf(qq.y, uf[2 * i].y, ar));
-                ai = fmaf(qq.x, uf[2 * i].y, fmaf(-qq.y, uf[2 * i].x, ai));
-                ar = fmaf(qq.z, uf[2 * i + 1].x, fmaf(qq.w, uf[2 * i + 1].y, ar));
-                ai = fmaf(qq.z, uf[2 * i + 1].y, fmaf(-qq.w, uf[2 * i + 1].x, ai));
-                br = fmaf(qq.x, wf[2 * i].x, fmaf(qq.y, wf[2 * i].y, br));
-                bi = fmaf(qq.x, wf[2 * i].y, fmaf(-qq.y, wf[2 * i].x, bi));
-                br = fmaf(qq.z, wf[2 * i + 1].x, fmaf(qq.w, wf[2 * i + 1].y, br));
-                bi = fmaf(qq.z, wf[2 * i + 1].y, fmaf(-qq.w, wf[2 * i + 1].x, bi));
+            for (int h = 0; h < 2; h++) {  // two batches of 8 loads in flight
+                float4 qq[DOTB_FL / 2];
+#pragma unroll
+                for (int i = 0; i < DOTB_FL / 2; i++) {
+                    const int rl = 64 * (h * (DOTB_FL / 2) + i) + 2 * lane;  // local row (even)
+                    qq[i] = (full || base + rl < N) ? __ldg(q + (rl >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int i = 0; i < DOTB_FL / 2; i++) {
+                    const int rl = 64 * (h * (DOTB_FL / 2) + i) + 2 * lane;
+                    const float4 x0 = s_uw[rl], x1 = s_uw[rl + 1];
+                    const float4 qv = qq[i];
+                    // conj(q) * u and conj(q) * w for rows rl, rl+1
+                    ar = fmaf(qv.x, x0.x, fmaf(qv.y, x0.y, ar));
+                    ai = fmaf(qv.x, x0.y, fmaf(-qv.y, x0.x, ai));
+                    br = fmaf(qv.x, x0.z, fmaf(qv.y, x0.w, br));
+                    bi = fmaf(qv.x, x0.w, fmaf(-qv.y, x0.z, bi));
+                    ar = fmaf(qv.z, x1.x, fmaf(qv.w, x1.y, ar));
+                    ai = fmaf(qv.z, x1.y, fmaf(-qv.w, x1.x, ai));
+                    br = fmaf(qv.z, x1.z, fmaf(qv.w, x1.w, br));
+                    bi = fmaf(qv.z, x1.w, fmaf(-qv.w, x1.z, bi));
+                }
             }
             ar = warp_sum(ar);
             ai = warp_sum(ai);
@@ -127,7 +146,12 @@ __global__ void __launch_bounds__(DOT_THREADS) k_gs_dot(BatchDev B, int j) {
     }
     __syncthreads();
     double2* out = B.part + ((size_t)s * B.G + blockIdx.x) * B.pstride;
-    for (int o = tid; o < 2 * p + 3; o += DOT_THREADS) out[o] = acc[o];
+    // columns of this group (and the scalars from group 0); other groups write theirs
+    for (int c = cg + CG * tid; c < p; c += CG * DOT_THREADS) {
+        out[c] = acc[c];
+        out[p + c] = acc[p + c];
+    }
+    if (cg == 0 && tid < 3) out[2 * p + tid] = acc[2 * p + tid];
 }
 
 // sum the per-block partials: dots[s][o] = sum_g part[s][g][o]
@@ -350,21 +374,29 @@ __global__ void __launch_bounds__(256) k_gs_update(BatchDev B, int j) {
     if (!solve_in_step(d, j)) return;
     const int p = solve_p(d, j);
     const size_t N = B.N;
-    __shared__ float2 s_ap[OVL_MAXCOL];
-    __shared__ float2 s_gh[OVL_MAXCOL];
-    __shared__ float2 s_gl[OVL_MAXCOL];
+    extern __shared__ float2 upd_dyn[];  // ap, gh, gl (pmax each), then column pointers
+    float2* s_ap = upd_dyn;
+    float2* s_gh = s_ap + B.pmax;
+    float2* s_gl = s_gh + B.pmax;
+    const float2** s_qh = (const float2**)(s_gl + B.pmax);
+    const float2** s_ql = s_qh + OVL_MAXPTR;
     __shared__ float4 red_q[8][UPD_RB / 2];   // sq for row pairs
     __shared__ float4 red_g[8][UPD_RB];       // (s.x, s.y, t.x, t.y) per row
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nptr = d.nptr;
     for (int c = tid; c < p; c += 256) {
         s_ap[c] = d.ap[c];
         s_gh[c] = d.gh[c];
         if (DF) s_gl[c] = d.gl[c];
     }
+    for (int c = tid; c < nptr && c < p; c += 256) {
+        s_qh[c] = d.qhi[c];
+        if (DF) s_ql[c] = d.qlo[c];
+    }
     const double inv_nu = d.scal[0];
     const double2 cu = make_double2(d.scal[1], d.scal[2]);
-    float2* qh_out = (float2*)d.qhi[p];
-    float2* ql_out = DF ? (float2*)d.qlo[p] : nullptr;
+    float2* qh_out = (float2*)(p < nptr ? d.qhi[p] : d.vhi + (size_t)(p - nptr) * N);
+    float2* ql_out = DF ? (float2*)(p < nptr ? d.qlo[p] : d.vlo + (size_t)(p - nptr) * N) : nullptr;
     __syncthreads();
     for (size_t base = (size_t)blockIdx.x * UPD_RB; base < N; base += (size_t)gridDim.x * UPD_RB) {
         const bool full = base + UPD_RB <= N;
@@ -375,32 +407,50 @@ __global__ void __launch_bounds__(256) k_gs_update(BatchDev B, int j) {
             sq[i] = make_float2(0.f, 0.f);
             dfacc_zero(sg[i]);
         }
-        for (int c = warp; c < p; c += 8) {
-            const float4* __restrict__ qh = (const float4*)d.qhi[c];
-            const float4* __restrict__ ql = DF ? (const float4*)d.qlo[c] : nullptr;
-            const float2 apc = s_ap[c], ghc = s_gh[c];
-            const float2 glc = DF ? s_gl[c] : make_float2(0.f, 0.f);
+        // columns in descending order (pass A read them ascending: the most
+        // recently read ones may still be in L2); two columns per iteration
+        for (int c0 = p - 1 - warp; c0 >= 0; c0 -= 16) {
+            float4 h4[2][UPD_RPL / 2], l4[2][UPD_RPL / 2];
 #pragma unroll
-            for (int i = 0; i < UPD_RPL / 2; i++) {
-                size_t r = base + 64 * i + 2 * lane;
-                bool ok = full || r < N;
-                float4 h4 = ok ? __ldg(qh + (r >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
-                float4 l4 = (DF && ok) ? __ldg(ql + (r >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
-                float2 h0 = make_float2(h4.x, h4.y), h1 = make_float2(h4.z, h4.w);
-                float2 l0 = make_float2(l4.x, l4.y), l1 = make_float2(l4.z, l4.w);
-                // sq += q * ap   (FP32; |ap| is tiny)
-                sq[2 * i].x = fmaf(h0.x, apc.x, fmaf(-h0.y, apc.y, sq[2 * i].x));
-                sq[2 * i].y = fmaf(h0.x, apc.y, fmaf(h0.y, apc.x, sq[2 * i].y));
-                sq[2 * i + 1].x = fmaf(h1.x, apc.x, fmaf(-h1.y, apc.y, sq[2 * i + 1].x));
-                sq[2 * i + 1].y = fmaf(h1.x, apc.y, fmaf(h1.y, apc.x, sq[2 * i + 1].y));
-                if (DF) {
-                    dfacc_mac(sg[2 * i], h0, l0, ghc, glc);
-                    dfacc_mac(sg[2 * i + 1], h1, l1, ghc, glc);
-                } else {
-                    sg[2 * i].s.x = fmaf(h0.x, ghc.x, fmaf(-h0.y, ghc.y, sg[2 * i].s.x));
-                    sg[2 * i].s.y = fmaf(h0.x, ghc.y, fmaf(h0.y, ghc.x, sg[2 * i].s.y));
-                    sg[2 * i + 1].s.x = fmaf(h1.x, ghc.x, fmaf(-h1.y, ghc.y, sg[2 * i + 1].s.x));
-                    sg[2 * i + 1].s.y = fmaf(h1.x, ghc.y, fmaf(h1.y, ghc.x, sg[2 * i + 1].s.y));
+            for (int bb = 0; bb < 2; bb++) {
+                const int c = c0 - 8 * bb;
+                const float4* __restrict__ qh =
+                    c >= 0 ? (const float4*)(c < nptr ? s_qh[c] : d.vhi + (size_t)(c - nptr) * N) : nullptr;
+                const float4* __restrict__ ql =
+                    (DF && c >= 0) ? (const float4*)(c < nptr ? s_ql[c] : d.vlo + (size_t)(c - nptr) * N) : nullptr;
+#pragma unroll
+                for (int i = 0; i < UPD_RPL / 2; i++) {
+                    size_t r = base + 64 * i + 2 * lane;
+                    bool ok = qh && (full || r < N);
+                    h4[bb][i] = ok ? __ldg(qh + (r >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    l4[bb][i] = (DF && ok) ? __ldg(ql + (r >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int bb = 0; bb < 2; bb++) {
+                const int c = c0 - 8 * bb;
+                if (c < 0) continue;
+                const float2 apc = s_ap[c], ghc = s_gh[c];
+                const float2 glc = DF ? s_gl[c] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < UPD_RPL / 2; i++) {
+                    const float4 hv = h4[bb][i], lv = l4[bb][i];
+                    float2 h0 = make_float2(hv.x, hv.y), h1 = make_float2(hv.z, hv.w);
+                    float2 l0 = make_float2(lv.x, lv.y), l1 = make_float2(lv.z, lv.w);
+                    // sq += q * ap   (FP32; |ap| is tiny)
+                    sq[2 * i].x = fmaf(h0.x, apc.x, fmaf(-h0.y, apc.y, sq[2 * i].x));
+                    sq[2 * i].y = fmaf(h0.x, apc.y, fmaf(h0.y, apc.x, sq[2 * i].y));
+                    sq[2 * i + 1].x = fmaf(h1.x, apc.x, fmaf(-h1.y, apc.y, sq[2 * i + 1].x));
+                    sq[2 * i + 1].y = fmaf(h1.x, apc.y, fmaf(h1.y, apc.x, sq[2 * i + 1].y));
+                    if (DF) {
+                        dfacc_mac(sg[2 * i], h0, l0, ghc, glc);
+                        dfacc_mac(sg[2 * i + 1], h1, l1, ghc, glc);
+                    } else {
+                        sg[2 * i].s.x = fmaf(h0.x, ghc.x, fmaf(-h0.y, ghc.y, sg[2 * i].s.x));
+                        sg[2 * i].s.y = fmaf(h0.x, ghc.y, fmaf(h0.y, ghc.x, sg[2 * i].s.y));
+                        sg[2 * i + 1].s.x = fmaf(h1.x, ghc.x, fmaf(-h1.y, ghc.y, sg[2 * i + 1].s.x));
+                        sg[2 * i + 1].s.y = fmaf(h1.x, ghc.y, fmaf(h1.y, ghc.x, sg[2 * i + 1].s.y));
+                    }
                 }
             }
         }
@@ -589,8 +639,9 @@ __global__ void __launch_bounds__(256) k_start(BatchDev B, const double* beta2, 
         return;
     }
     double inv = 1.0 / sqrt(b2);
-    float2* qh = (float2*)d.qhi[d.m_q];
-    float2* ql = DF ? (float2*)d.qlo[d.m_q] : nullptr;
+    const int c0 = d.m_q;
+    float2* qh = (float2*)(c0 < d.nptr ? d.qhi[c0] : d.vhi + (size_t)(c0 - d.nptr) * B.N);
+    float2* ql = DF ? (float2*)(c0 < d.nptr ? d.qlo[c0] : d.vlo + (size_t)(c0 - d.nptr) * B.N) : nullptr;
     for (size_t r = blockIdx.x * (size_t)256 + threadIdx.x; r < B.N; r += (size_t)gridDim.x * 256) {
         double2 x = d.u[r];
         double2 v = make_double2(x.x * inv, x.y * inv);
@@ -605,7 +656,7 @@ __global__ void __launch_bounds__(256) k_start(BatchDev B, const double* beta2, 
 }  // namespace
 
 int ovl_gs_grid(ovl_lattice lat) {
-    size_t blocks = (lat->N + DOT_RB - 1) / DOT_RB;
+    size_t blocks = (lat->N + DOTB_RB - 1) / DOTB_RB;
     size_t g = (size_t)lat->num_sms * 2;
     if (blocks < g) g = blocks;
     if (g < 1) g = 1;
@@ -613,7 +664,12 @@ int ovl_gs_grid(ovl_lattice lat) {
 }
 
 int ovl_gs_dot(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
-    dim3 grid(b.G, b.nsolve);
+    // column groups: enough CTAs to cover every SM about twice
+    int cgs = (2 * lat->num_sms + b.G * b.nsolve - 1) / (b.G * b.nsolve);
+    if (cgs < 1) cgs = 1;
+    if (cgs > 8) cgs = 8;
+    if (b.pmax < 8 * cgs) cgs = std::max(1, b.pmax / 8);
+    dim3 grid(b.G, b.nsolve, cgs);
     k_gs_dot<<<grid, DOT_THREADS, 0, st>>>(b, j);
     OVL_LAUNCH_CHECK(lat);
     return OVL_OK;
@@ -641,10 +697,17 @@ int ovl_gs_update(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
     if (blocks < g) g = blocks;
     dim3 grid((unsigned)g, b.nsolve);
     // the batch is homogeneous in precision (checked by the caller)
+    size_t dyn = (size_t)b.pmax * 3 * sizeof(float2) + 2 * OVL_MAXPTR * sizeof(void*);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_gs_update<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        cudaFuncSetAttribute(k_gs_update<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        attr_set = true;
+    }
     if (b.df)
-        k_gs_update<true><<<grid, 256, 0, st>>>(b, j);
+        k_gs_update<true><<<grid, 256, dyn, st>>>(b, j);
     else
-        k_gs_update<false><<<grid, 256, 0, st>>>(b, j);
+        k_gs_update<false><<<grid, 256, dyn, st>>>(b, j);
     OVL_LAUNCH_CHECK(lat);
     return OVL_OK;
 }

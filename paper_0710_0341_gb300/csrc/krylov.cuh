@@ -4,6 +4,7 @@
 #include "ovl_common.cuh"
 
 #define OVL_MAXCOL 960  // m + k + 1 (columns of the augmented basis) per solve
+#define OVL_MAXPTR 200  // columns addressed through pointers (the Schur vectors)
 
 // One solve of a batch. All pointers are device memory.
 //
@@ -17,6 +18,11 @@
 struct SolveDev {
     const float2* const* qhi;
     const float2* const* qlo;  // null in the mixed modes
+    // columns c >= nptr are contiguous: vhi + (c - nptr) * N (same for vlo);
+    // columns c < nptr (the Schur vectors) come from qhi/qlo
+    const float2* vhi;
+    const float2* vlo;
+    int nptr;
     double2* u;      // Arnoldi candidate (once orthogonalised, unnormalised)
     double2* w;      // A u
     double2* H;

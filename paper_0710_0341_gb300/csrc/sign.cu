@@ -107,7 +107,7 @@ extern "C" int ovl_set_deflation(ovl_lattice lat, double mu, double m_w, int sch
     if (!lat || !out || !S_or_R || !T) return ovl_fail(lat, OVL_EINVAL, "ovl_set_deflation: null argument");
     if (scheme != OVL_DEFL_SCHUR && scheme != OVL_DEFL_LR)
         return ovl_fail(lat, OVL_EINVAL, "ovl_set_deflation: scheme %d is not Schur or LR", scheme);
-    if (m < 1 || (size_t)m >= lat->N || m > 256) return ovl_fail(lat, OVL_EINVAL, "ovl_set_deflation: m=%d", m);
+    if (m < 1 || (size_t)m >= lat->N || m > 200) return ovl_fail(lat, OVL_EINVAL, "ovl_set_deflation: m=%d (1..200)", m);
     if (scheme == OVL_DEFL_LR && !L) return ovl_fail(lat, OVL_EINVAL, "ovl_set_deflation: LR needs L");
     if (scheme == OVL_DEFL_SCHUR && L) return ovl_fail(lat, OVL_EINVAL, "ovl_set_deflation: Schur takes no L");
     ovl_deflation d = new ovl_deflation_s();
@@ -382,6 +382,9 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         SolveDev& s = hs[i];
         s.qhi = p.qhi;
         s.qlo = df ? p.qlo : nullptr;
+        s.vhi = p.Vhi;
+        s.vlo = df ? p.Vlo : nullptr;
+        s.nptr = p.m_q;
         s.u = p.u;
         s.w = p.w;
         s.H = p.H;
