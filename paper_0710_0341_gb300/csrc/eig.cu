@@ -365,7 +365,7 @@ class Solver {
                     break;
             }
             bool done = nconv >= nw || pc < p;  // pc < p: exact invariant subspace
-            int qn = done ? nw : std::min(p - 2, nw + std::max((p - nw) / 2, nconv));
+            int qn = done ? nw : std::min(p - 2, nw + std::max((p - nw) / 3, nconv));
             if (qn < 1) qn = 1;
             // new basis columns V Z[:, 0:qn] and the start vector u/beta
             std::vector<double2*> ys(qn);
@@ -503,14 +503,16 @@ extern "C" int ovl_deflation_setup(ovl_lattice lat, double mu, double m_w, int s
     if (max_restarts <= 0) max_restarts = 1000;
     const size_t N = lat->N;
     int nev = m + std::max(8, m / 2);
-    int p = std::max(3 * nev, nev + 40);
+    int p = std::max(4 * nev, nev + 60);
     if ((size_t)p + 2 > N) {
         p = (int)N - 2;
         nev = std::min(nev, p / 2);
     }
     if (p > OVL_MAXCOL - 1) p = OVL_MAXCOL - 1;
     if (nev < m) return ovl_fail(lat, OVL_EINVAL, "ovl_deflation_setup: lattice too small for m=%d", m);
-    int runs = scheme == OVL_DEFL_LR ? 2 : 1;
+    // at mu = 0, H_w is Hermitian (H_w(mu)^dag = H_w(-mu)): left = right vectors
+    const bool hermitian = (mu == 0.0);
+    int runs = (scheme == OVL_DEFL_LR && !hermitian) ? 2 : 1;
     EigResult res[2];
     Mat Gm[2], Mm[2];
     Solver* sv[2] = {nullptr, nullptr};
@@ -564,6 +566,10 @@ extern "C" int ovl_deflation_setup(ovl_lattice lat, double mu, double m_w, int s
             }
         } else if (!rc) {
             // right vectors R, eigenvalues, and left vectors from A^dag = H_w(-mu)
+            if (hermitian) {
+                sv[1] = sv[0];
+                res[1] = res[0];
+            }
             Solver& s1 = *sv[1];
             if (cudaMalloc(&d->L_hi, N * m * sizeof(float2)) != cudaSuccess ||
                 cudaMalloc(&d->L_lo, N * m * sizeof(float2)) != cudaSuccess)
@@ -593,7 +599,7 @@ extern "C" int ovl_deflation_setup(ovl_lattice lat, double mu, double m_w, int s
                 std::vector<double2*> rr(m), ll(m);
                 for (int i = 0; i < m; i++) {
                     rr[i] = s0.Wf + N * i;
-                    ll[i] = s1.Wf + N * i;
+                    ll[i] = (hermitian ? s1.Vf : s1.Wf) + N * i;  // no aliasing when s1 == s0
                 }
                 Mat CL(nev, m);
                 for (int i = 0; i < m; i++)
@@ -644,6 +650,7 @@ extern "C" int ovl_deflation_setup(ovl_lattice lat, double mu, double m_w, int s
         }
         if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = ovl_fail(lat, OVL_ECUDA, "deflation setup: sync");
     }
+    if (sv[1] == sv[0]) sv[1] = nullptr;  // Hermitian case shared one run
     if (d && !rc) {
         d->setup_restarts = sv[0]->restarts + (sv[1] ? sv[1]->restarts : 0);
         d->setup_matvecs = sv[0]->matvecs + (sv[1] ? sv[1]->matvecs : 0);

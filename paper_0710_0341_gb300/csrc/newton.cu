@@ -348,8 +348,10 @@ int ovl_fmatvec_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int nmax,
 
 namespace {
 
+constexpr int NTD = 512;  // threads of the double-float kernel (16 warps to hide FP32 chains)
+
 template <bool SMEM>
-__global__ void __launch_bounds__(NT, 1) k_newton_df(NewtonDev* nds, int nsolve, int cpm) {
+__global__ void __launch_bounds__(NTD, 1) k_newton_df(NewtonDev* nds, int nsolve, int cpm) {
     extern __shared__ float4 dsm[];
     const int s = blockIdx.x / cpm;
     const int g = blockIdx.x % cpm;
@@ -366,16 +368,18 @@ __global__ void __launch_bounds__(NT, 1) k_newton_df(NewtonDev* nds, int nsolve,
     int* piv = (int*)(fcol + ((nr + 1) & ~1));
     int* pinv = piv + n;
     unsigned char* used = (unsigned char*)(pinv + n);
-    __shared__ float s_red[NT / 32];
-    __shared__ int s_idx[NT / 32];
+    __shared__ float s_red[NTD / 32];
+    __shared__ int s_idx[NTD / 32];
     __shared__ float4 s_inv;
     __shared__ double s_logdet, s_c;
-    __shared__ float s_nrm[2][NT / 32];
+    __shared__ float s_nrm[2][NTD / 32];
+    __shared__ double s_cv[64];
+    __shared__ int s_cr[64];
     unsigned gen = 0;
     // X_0 = H (column-major FP64 input)
     for (int r = 0; r < nr; r++) {
         int i = g + cpm * r;
-        for (int l = tid; l < n; l += NT) X[(size_t)i * n + l] = dfc_pack(dfc_from(d.H[i + (size_t)l * d.ldH]));
+        for (int l = tid; l < n; l += NTD) X[(size_t)i * n + l] = dfc_pack(dfc_from(d.H[i + (size_t)l * d.ldH]));
     }
     bool scaling = true, converged = false;
     double prev_rel = 1e300;
@@ -385,9 +389,9 @@ __global__ void __launch_bounds__(NT, 1) k_newton_df(NewtonDev* nds, int nsolve,
         iter++;
         for (int r = 0; r < nr; r++) {
             int i = g + cpm * r;
-            for (int l = tid; l < n; l += NT) R[(size_t)r * n + l] = __ldcg(X + (size_t)i * n + l);
+            for (int l = tid; l < n; l += NTD) R[(size_t)r * n + l] = __ldcg(X + (size_t)i * n + l);
         }
-        for (int i = tid; i < n; i += NT) used[i] = 0;
+        for (int i = tid; i < n; i += NTD) used[i] = 0;
         if (tid == 0) s_logdet = 0.0;
         __syncthreads();
         int bad = 0;
@@ -395,7 +399,7 @@ __global__ void __launch_bounds__(NT, 1) k_newton_df(NewtonDev* nds, int nsolve,
             // best unused own row for column k (|hi|^2), published with its data
             float best = -1.f;
             int br = -1;
-            for (int r = tid; r < nr; r += NT) {
+            for (int r = tid; r < nr; r += NTD) {
                 int i = g + cpm * r;
                 if (used[i]) continue;
                 float4 v = R[(size_t)r * n + k];
@@ -420,25 +424,31 @@ __global__ void __launch_bounds__(NT, 1) k_newton_df(NewtonDev* nds, int nsolve,
             __syncthreads();
             best = s_red[0];
             br = s_idx[0];
-            for (int w = 1; w < NT / 32; w++)
+            for (int w = 1; w < NTD / 32; w++)
                 if (s_red[w] > best || (s_red[w] == best && s_idx[w] >= 0 && (br < 0 || s_idx[w] < br))) {
                     best = s_red[w];
                     br = s_idx[w];
                 }
             const int slot = (k & 1) * cpm + g;
             if (br >= 0)
-                for (int l = tid; l < n; l += NT) d.crow[(size_t)slot * n + l] = R[(size_t)br * n + l];
+                for (int l = tid; l < n; l += NTD) d.crow[(size_t)slot * n + l] = R[(size_t)br * n + l];
             if (tid == 0) {
                 d.cand_val[slot] = br >= 0 ? (double)best : -1.0;
                 d.cand_row[slot] = br >= 0 ? g + cpm * br : 0x7fffffff;
             }
             if (!group_sync(d, gen, cpm)) return;
-            // winner (same choice in every CTA: largest |pivot|, then smallest row)
+            // candidates in parallel (one L2 read per thread), then the winner
+            // (same choice in every CTA: largest |pivot|, then smallest row)
+            if (tid < cpm) {
+                s_cv[tid] = __ldcg(d.cand_val + (k & 1) * cpm + tid);
+                s_cr[tid] = __ldcg(d.cand_row + (k & 1) * cpm + tid);
+            }
+            __syncthreads();
             double bv = -1.0;
             int pr = 0x7fffffff, q = -1;
             for (int c = 0; c < cpm; c++) {
-                double v = ((volatile double*)d.cand_val)[(k & 1) * cpm + c];
-                int rw = ((volatile int*)d.cand_row)[(k & 1) * cpm + c];
+                double v = s_cv[c];
+                int rw = s_cr[c];
                 if (v > bv || (v == bv && rw < pr)) {
                     bv = v;
                     pr = rw;
@@ -459,27 +469,27 @@ __global__ void __launch_bounds__(NT, 1) k_newton_df(NewtonDev* nds, int nsolve,
                 piv[k] = pr;
             }
             // f values of own rows before they change
-            for (int r = tid; r < nr; r += NT) fcol[r] = R[(size_t)r * n + k];
+            for (int r = tid; r < nr; r += NTD) fcol[r] = R[(size_t)r * n + k];
             __syncthreads();
             const dfc inv = dfc_unpack(s_inv);
-            for (int l = tid; l < n; l += NT)
+            for (int l = tid; l < n; l += NTD)
                 prow[l] = l == k ? s_inv : dfc_pack(dfc_mul(dfc_unpack(__ldcg(pw + l)), inv));
             __syncthreads();
             const int rp = (pr % cpm == g) ? (pr - g) / cpm : -1;  // own index of the pivot row
-            for (int r = 0; r < nr; r++) {
-                float4* row = R + (size_t)r * n;
-                if (r == rp) {
-                    for (int l = tid; l < n; l += NT) row[l] = prow[l];
-                    continue;
-                }
-                const dfc f = dfc_unpack(fcol[r]);
-                if (f.hi.x == 0.f && f.hi.y == 0.f && f.lo.x == 0.f && f.lo.y == 0.f) continue;
-                for (int l = tid; l < n; l += NT) {
-                    dfc pl = dfc_unpack(prow[l]);
-                    if (l == k)
-                        row[l] = dfc_pack(dfc_fms(dfc_zero(), f, pl));
-                    else
-                        row[l] = dfc_pack(dfc_fms(dfc_unpack(row[l]), f, pl));
+            if (rp >= 0)
+                for (int l = tid; l < n; l += NTD) R[(size_t)rp * n + l] = prow[l];
+            // two rows per pass: independent dependency chains per thread
+            for (int r0 = 0; r0 < nr; r0 += 2) {
+                const bool two = r0 + 1 < nr;
+                const bool a_on = r0 != rp, b_on = two && (r0 + 1 != rp);
+                const dfc fa = dfc_unpack(fcol[r0]);
+                const dfc fb = two ? dfc_unpack(fcol[r0 + 1]) : dfc_zero();
+                float4* ra = R + (size_t)r0 * n;
+                float4* rb = R + (size_t)(r0 + 1) * n;
+                for (int l = tid; l < n; l += NTD) {
+                    const dfc pl = dfc_unpack(prow[l]);
+                    if (a_on) ra[l] = dfc_pack(dfc_fms(l == k ? dfc_zero() : dfc_unpack(ra[l]), fa, pl));
+                    if (b_on) rb[l] = dfc_pack(dfc_fms(l == k ? dfc_zero() : dfc_unpack(rb[l]), fb, pl));
                 }
             }
             __syncthreads();
@@ -488,7 +498,7 @@ __global__ void __launch_bounds__(NT, 1) k_newton_df(NewtonDev* nds, int nsolve,
             if (tid == 0 && g == 0) atomicExch(d.status, OVL_ENOCONV);
             return;
         }
-        for (int k = tid; k < n; k += NT) pinv[piv[k]] = k;
+        for (int k = tid; k < n; k += NTD) pinv[piv[k]] = k;
         if (tid == 0) s_c = scaling ? exp(-s_logdet / n) : 1.0;
         __syncthreads();
         // inverse: Xinv[pinv(q)][piv[j]] = St[q][j] for the own stored rows q;
@@ -499,7 +509,7 @@ __global__ void __launch_bounds__(NT, 1) k_newton_df(NewtonDev* nds, int nsolve,
             const int qrow = g + cpm * r;
             const int i = pinv[qrow];
             float4* xr = X + (size_t)i * n;
-            for (int j = tid; j < n; j += NT) {
+            for (int j = tid; j < n; j += NTD) {
                 const int l = piv[j];
                 dfc xo = dfc_unpack(__ldcg(xr + l));  // rows of X move between CTAs
                 dfc a = dfc_unpack(R[(size_t)r * n + j]);
@@ -522,7 +532,7 @@ __global__ void __launch_bounds__(NT, 1) k_newton_df(NewtonDev* nds, int nsolve,
         __syncthreads();
         if (tid == 0) {
             double a = 0.0, b = 0.0;
-            for (int w = 0; w < NT / 32; w++) {
+            for (int w = 0; w < NTD / 32; w++) {
                 a += s_nrm[0][w];
                 b += s_nrm[1][w];
             }
@@ -530,10 +540,17 @@ __global__ void __launch_bounds__(NT, 1) k_newton_df(NewtonDev* nds, int nsolve,
             d.red[2 * g + 1] = b;
         }
         if (!group_sync(d, gen, cpm)) return;
+        if (tid < cpm) {
+            s_cv[tid] = __ldcg(d.red + 2 * tid);
+            s_cr[tid] = 0;
+        }
+        __shared__ double s_nn[64];
+        if (tid < cpm) s_nn[tid] = __ldcg(d.red + 2 * tid + 1);
+        __syncthreads();
         double D = 0.0, Nn = 0.0;
         for (int c2 = 0; c2 < cpm; c2++) {
-            D += ((volatile double*)d.red)[2 * c2];
-            Nn += ((volatile double*)d.red)[2 * c2 + 1];
+            D += s_cv[c2];
+            Nn += s_nn[c2];
         }
         const double rel_step = sqrt(D) / sqrt(Nn);
         const bool unscaled = !scaling;
@@ -582,12 +599,12 @@ int ovl_newton_df_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int nma
     const void* fn = smem_rows ? (const void*)k_newton_df<true> : (const void*)k_newton_df<false>;
     OVL_CUDA_TRY(lat, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessorWithFlags(&per_sm, fn, NT, smem, cudaOccupancyDefault);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessorWithFlags(&per_sm, fn, NTD, smem, cudaOccupancyDefault);
     if (per_sm < 1 || (long)nsolve * cpm > (long)lat->num_sms * per_sm)
         return ovl_fail(lat, OVL_EINVAL, "Newton batch of %d x %d blocks exceeds co-residency (%d per SM)", nsolve,
                         cpm, per_sm);
     void* args[] = {(void*)&nd_dev, (void*)&nsolve, (void*)&cpm};
-    OVL_CUDA_TRY(lat, cudaLaunchCooperativeKernel(fn, dim3(nsolve * cpm), dim3(NT), args, smem, st));
+    OVL_CUDA_TRY(lat, cudaLaunchCooperativeKernel(fn, dim3(nsolve * cpm), dim3(NTD), args, smem, st));
     lat->launches++;
     return OVL_OK;
 }

@@ -1,0 +1,45 @@
+"""One batch of the 8^4 sign-function workload, for kernel profiling.
+
+Runs ovl_sign_apply once for 8 solves (mu in {0, 0.1, 0.3, 0.6} x Schur/LR,
+k = 400, m = 30, FP64 mode) with deflation data imported from a seeded
+orthonormal block (the kernels' work does not depend on the eigenvectors,
+so the expensive eigensolver setup is skipped), inside an NVTX range
+"sign_batch". Used as the command under ncu, e.g.
+
+    ncu --set full --clock-control none -k regex:k_gs_update -s 200 -c 1 \\
+        python -m paper_0710_0341_gb300.profile_case
+"""
+import numpy as np
+import torch
+
+from paper_0710_0341_gb300 import build, ovl, synth
+
+
+def main():
+    build.build()
+    dims, m = (8, 8, 8, 8), 30
+    N = 12 * 8 ** 4
+    U = synth.random_su3_field(dims, 0.4, 0)
+    h = ovl.ovl_create_lattice(dims)
+    ovl.ovl_set_links(h, torch.from_numpy(U).cuda())
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.standard_normal((N, m)) + 1j * rng.standard_normal((N, m)))
+    cols = np.ascontiguousarray(Q.T.reshape((m,) + synth.lattice_shape(dims) + (4, 3)))
+    lam = np.linspace(0.17, 0.2, m).astype(complex)
+    T = np.diag(lam)
+    mus = [0.0, 0.1, 0.3, 0.6]
+    defl = [ovl.ovl_set_deflation(h, mu, -1.0, ovl.OVL_DEFL_SCHUR, m, cols, T.ravel(order="F").copy(), None)
+            for mu in mus]
+    defl += [ovl.ovl_set_deflation(h, mu, -1.0, ovl.OVL_DEFL_LR, m, cols, lam, cols) for mu in mus]
+    b = torch.from_numpy(np.stack([synth.gaussian_source(dims, 1)] * 8)).cuda()
+    y = torch.zeros_like(b)
+    params = [dict(mu=mu, m_w=-1.0, k=400) for mu in mus] * 2
+    torch.cuda.nvtx.range_push("sign_batch")
+    infos = ovl.ovl_sign_apply(h, params, defl, b, y)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print("profile case done; newton iterations", [i["newton_iters"] for i in infos])
+
+
+if __name__ == "__main__":
+    main()
