@@ -73,6 +73,15 @@ typedef struct {
     int    newton_max_iter;  /* <= 0: default 100 */
     double newton_tol;       /* <= 0: default 1e-13 (relative Frobenius step) */
     int    newton_fp64;      /* 0: double-float Gauss-Jordan (default); 1: FP64 Gauss-Jordan */
+    /* Adaptive Krylov depth (not in the paper): with adapt_every = d > 0 the
+     * solve starts checking at depth k and then every d steps up to k_max:
+     * the estimate est_j = |g_j - (g_{j-d}; 0)| / |g_j| compares the
+     * small-space coefficient vectors of successive approximations
+     * (g = sgn(H) c, the coordinates of y in the orthonormal basis), and the
+     * solve stops at the first j with est_j <= tol / 10. */
+    int    adapt_every;      /* 0: fixed k */
+    int    k_max;            /* upper bound of the adaptive depth (>= k) */
+    double tol;              /* target relative error of y (default 1e-8) */
 } ovl_sign_params;
 
 typedef struct {
@@ -82,6 +91,7 @@ typedef struct {
     int    newton_iters;  /* scaled Newton iterations for sgn of the small matrix */
     double beta;          /* |x_perp| or |x_minus|: norm of the Krylov start vector */
     double beta_k;        /* H_{k+1,k}, the last Arnoldi residual norm */
+    double err_est;       /* last adaptive estimate (0 when k was fixed) */
 } ovl_sign_info;
 
 /* ---- lattice and links ------------------------------------------------ */

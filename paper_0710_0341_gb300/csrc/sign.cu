@@ -189,6 +189,11 @@ namespace {
 
 struct SolvePlan {
     int m_q = 0, m_defl = 0, scheme = OVL_DEFL_NONE, k = 0, ldH = 0, nmax = 0;
+    int adapt = 0, k_first = 0;   // adaptive depth: check interval and first check
+    double tol = 1e-8, err_est = 0.0;
+    std::vector<double2> g_prev;  // coefficients at the previous check
+    double2 *H_est = nullptr, *g_est = nullptr;
+    float2* H32_est = nullptr;
     ovl_deflation d = nullptr;
     // device pieces
     float2 *Vhi = nullptr, *Vlo = nullptr;
@@ -234,8 +239,13 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         if (!(q.m_w > -4.0 + 1e-12) || !(q.mu == q.mu) || fabs(q.mu) > 50.0)
             return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: solve %d: bad mu/m_w", i);
         if (q.k < 1) return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: solve %d: k=%d < 1", i, q.k);
+        if (q.adapt_every < 0 || (q.adapt_every > 0 && q.k_max < q.k))
+            return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: solve %d: adaptive needs k_max >= k", i);
         SolvePlan& p = P[i];
-        p.k = q.k;
+        p.k = q.adapt_every > 0 ? q.k_max : q.k;
+        p.adapt = q.adapt_every;
+        p.k_first = q.k;
+        p.tol = q.tol > 0 ? q.tol : 1e-8;
         if (defl && defl[i]) {
             ovl_deflation d = defl[i];
             if (d->lat != lat) return ovl_fail(lat, OVL_EINVAL, "solve %d: deflation of another lattice", i);
@@ -304,6 +314,11 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             t(p.pu_lo, md);
             t(p.gc_hi, nm + md);
             t(p.gc_lo, nm + md);
+            if (p.adapt) {
+                t(p.H_est, ld * ld);
+                t(p.H32_est, ld * ld);
+                t(p.g_est, nm + md);
+            }
         }
         c.take<char>(0);
         return c.off;
@@ -313,6 +328,7 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     {
         Carve c{nullptr};
         c.off = per;
+        c.take<SolveDev>(nsolve);
         c.take<SolveDev>(nsolve);
         c.take<NewtonDev>(nsolve);
         c.take<ProjDev>(nsolve);
@@ -341,6 +357,7 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     Carve c{base};
     c.off = per;
     SolveDev* d_sd = c.take<SolveDev>(nsolve);
+    SolveDev* d_sd_est = c.take<SolveDev>(nsolve);
     NewtonDev* d_nd = c.take<NewtonDev>(nsolve);
     ProjDev* d_pd = c.take<ProjDev>(nsolve);
     GemvDev* d_gd = c.take<GemvDev>(nsolve);
@@ -524,6 +541,162 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     const int links = prec == OVL_PREC_FP64 ? OVL_LINKS_F64 : prec == OVL_PREC_MIXED ? OVL_LINKS_F32 : OVL_LINKS_R12;
     const double site_bytes = 2.0 * 12 * 16 + 4.0 * (links == OVL_LINKS_F64 ? 144 : links == OVL_LINKS_F32 ? 72 : 48);
     const double qbytes = df ? 16.0 : 8.0;
+    bool any_adapt = false;
+    for (int i = 0; i < nsolve; i++) any_adapt = any_adapt || P[i].adapt > 0;
+    // accurate Galerkin correction of the last column (FP64 projection of u)
+    // for the solves whose descriptor in sdev has fin set; H as in sdev
+    auto final_pass = [&](SolveDev* sdev, const std::vector<int>& ncol) -> int {
+        std::vector<ProjDev> pd(nsolve);
+        int maxcol = 0;
+        for (int i = 0; i < nsolve; i++) {
+            ProjDev& q = pd[i];
+            q.qhi = P[i].qhi;
+            q.qlo = P[i].qlo;
+            q.x = P[i].u;
+            q.out = P[i].dots;
+            q.coef = nullptr;
+            q.ncol = ncol[i];
+            maxcol = std::max(maxcol, q.ncol);
+        }
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_pd, pd.data(), nsolve * sizeof(ProjDev), cudaMemcpyHostToDevice, st));
+        BatchDev b2 = bd;
+        b2.sd = sdev;
+        b2.pmax = maxcol;
+        double fb = 0.0;
+        for (int i = 0; i < nsolve; i++) fb += (double)pd[i].ncol * N * 16.0 + N * 16.0;
+        ProfScope pf(lat, 6, fb, st);
+        if (int rc = ovl_gs_final(lat, b2, d_pd, maxcol, st)) return rc;
+        pf.end(st);
+        OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));  // pd must outlive the copy
+        return OVL_OK;
+    };
+    // scaled Newton on H[0:n, 0:n] of each solve with n[i] > 0; g = F c
+    std::vector<NewtonDev> nd(nsolve);
+    auto newton = [&](const std::vector<const double2*>& Hs, const std::vector<int>& nn,
+                      const std::vector<double2*>& gout) -> int {
+        int nmax_run = 0, any_run = 0;
+        for (int i = 0; i < nsolve; i++) {
+            SolvePlan& p = P[i];
+            NewtonDev& q = nd[i];
+            int n = nn[i];
+            q = NewtonDev();
+            q.H = Hs[i];
+            q.ldH = p.ldH;
+            q.n = n;
+            q.run = n > 0 ? 1 : 0;
+            q.max_iter = params[i].newton_max_iter > 0 ? params[i].newton_max_iter : 100;
+            q.tol = params[i].newton_tol > 0 ? params[i].newton_tol : 1e-13;
+            q.X = p.X;
+            q.W = p.W;
+            q.cand_val = p.cand_val;
+            q.cand_row = p.cand_row;
+            q.red = p.red;
+            q.bar = p.bar;
+            q.status = p.nstat;
+            q.iters = p.iters;
+            q.cvec = p.cvec;
+            q.gout = gout[i];
+            q.df = params[0].newton_fp64 ? 0 : 1;
+            q.crow = p.crow;
+            q.Wg = (float4*)p.W;
+            if (q.run) {
+                any_run = 1;
+                nmax_run = std::max(nmax_run, n);
+            }
+            // coefficient vector: Schur (S^dag b; beta e_1), otherwise beta e_1
+            std::vector<double2> cv(std::max(1, n), make_double2(0.0, 0.0));
+            if (p.scheme == OVL_DEFL_SCHUR)
+                for (int t = 0; t < p.m_q && t < n; t++)
+                    cv[t] = make_double2(c1[i][t].x + c2[i][t].x, c1[i][t].y + c2[i][t].y);
+            if (n > p.m_q) cv[p.m_q] = make_double2(beta[i], 0.0);
+            OVL_CUDA_TRY(lat,
+                         cudaMemcpyAsync(p.cvec, cv.data(), std::max(1, n) * sizeof(double2), cudaMemcpyHostToDevice, st));
+            OVL_CUDA_TRY(lat, cudaMemsetAsync(p.bar, 0, sizeof(unsigned), st));
+            OVL_CUDA_TRY(lat, cudaMemsetAsync(p.nstat, 0, sizeof(int), st));
+            OVL_CUDA_TRY(lat, cudaMemsetAsync(p.iters, 0, sizeof(int), st));
+            OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
+        }
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_nd, nd.data(), nsolve * sizeof(NewtonDev), cudaMemcpyHostToDevice, st));
+        if (any_run) {
+            int cpm_run = ovl_newton_cpm(lat, nsolve, nmax_run);
+            (void)cpm;
+            ProfScope pn(lat, 5, 0.0, st);
+            if (params[0].newton_fp64) {
+                if (int rc = ovl_newton_launch(lat, d_nd, nsolve, cpm_run, st)) return rc;
+            } else {
+                int cpm_df = 1, smem_rows = 0;
+                ovl_newton_df_plan(lat, nsolve, nmax_run, &cpm_df, &smem_rows);
+                if (int rc = ovl_newton_df_launch(lat, d_nd, nsolve, nmax_run, cpm_df, smem_rows, st)) return rc;
+            }
+            if (int rc = ovl_fmatvec_launch(lat, d_nd, nsolve, nmax_run, st)) return rc;
+            pn.end(st);
+        }
+        OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
+        return OVL_OK;
+    };
+    // adaptive depth: estimate from the coefficients of the approximation at
+    // depth j (H snapshot, accurate last-column correction on the copy, Newton)
+    auto adaptive_check = [&](int j) -> int {
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(hs.data(), d_sd, nsolve * sizeof(SolveDev), cudaMemcpyDeviceToHost, st));
+        OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
+        std::vector<SolveDev> he = hs;
+        std::vector<int> ncol(nsolve, 0), nn(nsolve, 0);
+        std::vector<const double2*> Hs(nsolve, nullptr);
+        std::vector<double2*> go(nsolve, nullptr);
+        bool any = false;
+        for (int i = 0; i < nsolve; i++) {
+            SolvePlan& p = P[i];
+            bool on = p.adapt && hs[i].active && j <= p.k && j >= p.k_first && (j - p.k_first) % p.adapt == 0;
+            he[i].fin = on ? 1 : 0;
+            he[i].active = 0;
+            if (!on) continue;
+            any = true;
+            size_t hb = (size_t)p.ldH * p.ldH;
+            OVL_CUDA_TRY(lat, cudaMemcpyAsync(p.H_est, p.H, hb * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            OVL_CUDA_TRY(lat, cudaMemcpyAsync(p.H32_est, p.H32, hb * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+            he[i].H = p.H_est;
+            he[i].H32 = p.H32_est;
+            he[i].k_used = j;
+            ncol[i] = p.m_q + j;
+            nn[i] = p.m_q + j;
+            Hs[i] = p.H_est;
+            go[i] = p.g_est;
+        }
+        if (!any) return OVL_OK;
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_sd_est, he.data(), nsolve * sizeof(SolveDev), cudaMemcpyHostToDevice, st));
+        if (int rc = final_pass(d_sd_est, ncol)) return rc;
+        if (int rc = newton(Hs, nn, go)) return rc;
+        bool changed = false;
+        for (int i = 0; i < nsolve; i++) {
+            if (!nn[i]) continue;
+            SolvePlan& p = P[i];
+            std::vector<double2> g(nn[i]);
+            OVL_CUDA_TRY(lat, cudaMemcpy(g.data(), p.g_est, nn[i] * sizeof(double2), cudaMemcpyDeviceToHost));
+            int st_n = 0;
+            OVL_CUDA_TRY(lat, cudaMemcpy(&st_n, p.nstat, sizeof(int), cudaMemcpyDeviceToHost));
+            if (st_n) continue;  // no estimate from a failed small sign; keep going
+            if (!p.g_prev.empty()) {
+                double dn = 0.0, gn = 0.0;
+                for (size_t t = 0; t < g.size(); t++) {
+                    double2 a = g[t], b = t < p.g_prev.size() ? p.g_prev[t] : make_double2(0.0, 0.0);
+                    dn += (a.x - b.x) * (a.x - b.x) + (a.y - b.y) * (a.y - b.y);
+                    gn += a.x * a.x + a.y * a.y;
+                }
+                p.err_est = gn > 0 ? sqrt(dn / gn) : 0.0;
+                if (p.err_est <= 0.1 * p.tol) {
+                    p.k = j;  // converged: stop this solve here
+                    hs[i].k = j;
+                    changed = true;
+                }
+            }
+            p.g_prev = g;
+        }
+        if (changed)
+            for (int i = 0; i < nsolve; i++)
+                OVL_CUDA_TRY(lat, cudaMemcpyAsync(&d_sd[i].k, &P[i].k, sizeof(int), cudaMemcpyHostToDevice, st));
+        OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
+        return OVL_OK;
+    };
     for (int j = 1; j <= kmax; j++) {
         int pmax = 0, nact = 0;
         double colsum = 0.0;
@@ -533,6 +706,7 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
                 nact++;
                 colsum += P[i].m_q + j - 1;
             }
+        if (!nact) break;
         bd.pmax = pmax;
         da.j = j;
         // algorithmic bytes: stencil 960 B/site (FP64); pass A reads the FP32 high
@@ -552,90 +726,36 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         ProfScope p4(lat, 4, colsum * N * qbytes + nact * (3.0 * N * 16.0 + N * qbytes), st);
         if (int rc = ovl_gs_update(lat, bd, j, st)) return rc;
         p4.end(st);
+        if (any_adapt)
+            if (int rc = adaptive_check(j)) return rc;
     }
-    // accurate Galerkin correction of the last column (FP64 projection of u)
     OVL_CUDA_TRY(lat, cudaMemcpyAsync(hs.data(), d_sd, nsolve * sizeof(SolveDev), cudaMemcpyDeviceToHost, st));
     OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
     {
-        std::vector<ProjDev> pd(nsolve);
-        int maxcol = 0, pmax = 0;
-        for (int i = 0; i < nsolve; i++) {
-            ProjDev& q = pd[i];
-            q.qhi = P[i].qhi;
-            q.qlo = P[i].qlo;
-            q.x = P[i].u;
-            q.out = P[i].dots;
-            q.coef = nullptr;
-            q.ncol = hs[i].fin ? P[i].m_q + hs[i].k_used : 0;
-            maxcol = std::max(maxcol, q.ncol);
-            pmax = std::max(pmax, q.ncol);
-        }
-        OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_pd, pd.data(), nsolve * sizeof(ProjDev), cudaMemcpyHostToDevice, st));
-        bd.pmax = pmax;
-        double fb = 0.0;
-        for (int i = 0; i < nsolve; i++) fb += (double)pd[i].ncol * N * 16.0 + N * 16.0;
-        ProfScope pf(lat, 6, fb, st);
-        if (int rc = ovl_gs_final(lat, bd, d_pd, maxcol, st)) return rc;
-        pf.end(st);
+        std::vector<int> ncol(nsolve);
+        for (int i = 0; i < nsolve; i++) ncol[i] = hs[i].fin ? P[i].m_q + std::min(hs[i].k_used, P[i].k) : 0;
+        // a solve stopped by the adaptive check: its depth is k (the loop stopped there)
+        for (int i = 0; i < nsolve; i++)
+            if (hs[i].fin && P[i].k < hs[i].k_used) {
+                hs[i].k_used = P[i].k;
+                OVL_CUDA_TRY(lat, cudaMemcpyAsync(&d_sd[i].k_used, &P[i].k, sizeof(int), cudaMemcpyHostToDevice, st));
+            }
+        if (int rc = final_pass(d_sd, ncol)) return rc;
     }
     OVL_CUDA_TRY(lat, cudaMemcpyAsync(hs.data(), d_sd, nsolve * sizeof(SolveDev), cudaMemcpyDeviceToHost, st));
     OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
 
     // ---- small sign by Newton ----
-    std::vector<NewtonDev> nd(nsolve);
-    int nmax_run = 0, any_run = 0;
-    for (int i = 0; i < nsolve; i++) {
-        SolvePlan& p = P[i];
-        NewtonDev& q = nd[i];
-        int n = p.m_q + hs[i].k_used;
-        q.H = p.H;
-        q.ldH = p.ldH;
-        q.n = n;
-        q.run = (n > 0 && hs[i].status == 0) ? 1 : 0;
-        q.max_iter = params[i].newton_max_iter > 0 ? params[i].newton_max_iter : 100;
-        q.tol = params[i].newton_tol > 0 ? params[i].newton_tol : 1e-13;
-        q.X = p.X;
-        q.W = p.W;
-        q.cand_val = p.cand_val;
-        q.cand_row = p.cand_row;
-        q.red = p.red;
-        q.bar = p.bar;
-        q.status = p.nstat;
-        q.iters = p.iters;
-        q.cvec = p.cvec;
-        q.gout = p.gcomb;
-        q.df = params[0].newton_fp64 ? 0 : 1;
-        q.crow = p.crow;
-        q.Wg = (float4*)p.W;
-        if (q.run) {
-            any_run = 1;
-            nmax_run = std::max(nmax_run, n);
+    {
+        std::vector<const double2*> Hs(nsolve);
+        std::vector<int> nn(nsolve);
+        std::vector<double2*> go(nsolve);
+        for (int i = 0; i < nsolve; i++) {
+            Hs[i] = P[i].H;
+            nn[i] = hs[i].status == 0 ? P[i].m_q + hs[i].k_used : 0;
+            go[i] = P[i].gcomb;
         }
-        // coefficient vector: Schur (S^dag b; beta e_1), otherwise beta e_1
-        std::vector<double2> cv(std::max(1, n), make_double2(0.0, 0.0));
-        if (p.scheme == OVL_DEFL_SCHUR)
-            for (int t = 0; t < p.m_q; t++) cv[t] = make_double2(c1[i][t].x + c2[i][t].x, c1[i][t].y + c2[i][t].y);
-        if (n > p.m_q && hs[i].k_used > 0) cv[p.m_q] = make_double2(beta[i], 0.0);
-        OVL_CUDA_TRY(lat, cudaMemcpyAsync(p.cvec, cv.data(), std::max(1, n) * sizeof(double2), cudaMemcpyHostToDevice, st));
-        OVL_CUDA_TRY(lat, cudaMemsetAsync(p.bar, 0, sizeof(unsigned), st));
-        OVL_CUDA_TRY(lat, cudaMemsetAsync(p.nstat, 0, sizeof(int), st));
-        OVL_CUDA_TRY(lat, cudaMemsetAsync(p.iters, 0, sizeof(int), st));
-        OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
-    }
-    OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_nd, nd.data(), nsolve * sizeof(NewtonDev), cudaMemcpyHostToDevice, st));
-    if (any_run) {
-        int cpm_run = ovl_newton_cpm(lat, nsolve, nmax_run);
-        (void)cpm;
-        ProfScope pn(lat, 5, 0.0, st);
-        if (params[0].newton_fp64) {
-            if (int rc = ovl_newton_launch(lat, d_nd, nsolve, cpm_run, st)) return rc;
-        } else {
-            int cpm_df = 1, smem_rows = 0;
-            ovl_newton_df_plan(lat, nsolve, nmax_run, &cpm_df, &smem_rows);
-            if (int rc = ovl_newton_df_launch(lat, d_nd, nsolve, nmax_run, cpm_df, smem_rows, st)) return rc;
-        }
-        if (int rc = ovl_fmatvec_launch(lat, d_nd, nsolve, nmax_run, st)) return rc;
-        pn.end(st);
+        if (int rc = newton(Hs, nn, go)) return rc;
     }
     std::vector<int> nstat(nsolve, 0), nit(nsolve, 0);
     for (int i = 0; i < nsolve; i++) {
@@ -712,6 +832,7 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             double bk = 0.0;
             cudaMemcpy(&bk, P[i].scal + 4, sizeof(double), cudaMemcpyDeviceToHost);
             info[i].beta_k = bk;
+            info[i].err_est = P[i].err_est;
         }
     }
     ovl_prof_flush(lat);

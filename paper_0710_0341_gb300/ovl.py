@@ -29,12 +29,13 @@ class OvlError(RuntimeError):
 
 class ovl_sign_params(C.Structure):
     _fields_ = [("mu", C.c_double), ("m_w", C.c_double), ("k", C.c_int), ("prec", C.c_int),
-                ("newton_max_iter", C.c_int), ("newton_tol", C.c_double), ("newton_fp64", C.c_int)]
+                ("newton_max_iter", C.c_int), ("newton_tol", C.c_double), ("newton_fp64", C.c_int),
+                ("adapt_every", C.c_int), ("k_max", C.c_int), ("tol", C.c_double)]
 
 
 class ovl_sign_info(C.Structure):
     _fields_ = [("status", C.c_int), ("k_used", C.c_int), ("m_used", C.c_int), ("newton_iters", C.c_int),
-                ("beta", C.c_double), ("beta_k", C.c_double)]
+                ("beta", C.c_double), ("beta_k", C.c_double), ("err_est", C.c_double)]
 
 
 _lib = None
@@ -195,11 +196,14 @@ def ovl_sign_apply(h, params, defl, b, y, info=True):
         P[i].newton_max_iter = int(p.get("newton_max_iter", 0))
         P[i].newton_tol = float(p.get("newton_tol", 0.0))
         P[i].newton_fp64 = int(p.get("newton_fp64", 0))
+        P[i].adapt_every = int(p.get("adapt_every", 0))
+        P[i].k_max = int(p.get("k_max", 0))
+        P[i].tol = float(p.get("tol", 0.0))
     D = (_P * n)(*[(d.value if isinstance(d, _P) else d) if d is not None else None for d in (defl or [None] * n)])
     I = (ovl_sign_info * n)()
     rc = lib().ovl_sign_apply(h, n, P, D, _ptr(b), _ptr(y), I)
     infos = [dict(status=I[i].status, k_used=I[i].k_used, m_used=I[i].m_used, newton_iters=I[i].newton_iters,
-                  beta=I[i].beta, beta_k=I[i].beta_k) for i in range(n)]
+                  beta=I[i].beta, beta_k=I[i].beta_k, err_est=I[i].err_est) for i in range(n)]
     if rc != OVL_OK:
         msg = lib().ovl_last_error(h)
         err = OvlError(rc, (msg.decode() if msg else "") + f" infos={infos}")
