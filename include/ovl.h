@@ -185,6 +185,35 @@ int ovl_destroy_deflation(ovl_deflation d);
 int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params* params,
                    const ovl_deflation* defl, const double* b, double* y, ovl_sign_info* info);
 
+/* ---- learned (k, m) predictor (not in the paper) ---------------------- */
+
+/* A small MLP x (n_in) -> ReLU -> ReLU -> y (n_out), FP32 on the device, with
+ * its own forward, backward and Adam kernels. It predicts (log k, log(m+1))
+ * from solve features so the Krylov basis can be sized before a solve; the
+ * adaptive depth of ovl_sign_apply is the fallback. Parameters are one flat
+ * vector [W1 (n_h x n_in, row-major), b1, W2, b2, W3, b3]. Loss: mean of
+ * w (y - t)^2 with w = under_weight where y < t. Arrays: host or device.
+ * n_in <= 32, n_hidden a multiple of 32 in [32, 128], n_out <= 4. */
+typedef struct ovl_mlp_s* ovl_mlp;
+int ovl_mlp_create(int n_in, int n_hidden, int n_out, ovl_mlp* out);
+int ovl_mlp_destroy(ovl_mlp net);
+int ovl_mlp_num_params(ovl_mlp net, int* np);
+int ovl_mlp_set_params(ovl_mlp net, const float* theta);  /* also resets Adam state */
+int ovl_mlp_get_params(ovl_mlp net, float* theta);
+int ovl_mlp_forward(ovl_mlp net, const float* X, int batch, float* Y);       /* X: batch x n_in */
+int ovl_mlp_loss_grad(ovl_mlp net, const float* X, const float* T, int batch, float under_weight,
+                      float* loss, float* grad);                            /* grad: np floats */
+int ovl_mlp_train(ovl_mlp net, const float* X, const float* T, int batch, int steps, float lr,
+                  float under_weight, float* final_loss);                   /* full-batch Adam */
+const char* ovl_mlp_last_error(ovl_mlp net);
+
+/* Features for the predictor. ovl_link_spread: mean over links of
+ * 1 - Re tr U / 3. ovl_ritz_values: the k Ritz values of H_w(mu) from k
+ * Arnoldi steps (FP64 mode, no deflation) started at b (canonical spinor,
+ * host or device); out (host memory) receives k complex128 values. */
+int ovl_link_spread(ovl_lattice lat, double* spread);
+int ovl_ritz_values(ovl_lattice lat, double mu, double m_w, int k, const double* b, double* out);
+
 /* Kernel accounting for timing reports. ovl_launch_count: kernels launched
  * through this handle so far. ovl_profile(enable=1) clears and starts
  * per-kernel-class CUDA-event timing of ovl_sign_apply on the lattice's

@@ -97,7 +97,7 @@ class Solver {
     int p, nev;
     double mu, kappa;
     Dev mem;
-    float2 *Va_hi, *Va_lo, *Vb_hi, *Vb_lo;
+    float2 *Va_hi = nullptr, *Va_lo, *Vb_hi, *Vb_lo;
     double2 *u, *w, *tmp, *H, *dots, *dvec, *part, *Vf, *Wf, *gcoef;
     float2 *H32, *ap, *gh, *gl;
     double* scal;
@@ -111,6 +111,10 @@ class Solver {
     double* d_mu;
     int G, pstride;
     int restarts = 0, matvecs = 0;
+    int power = 2;            // operator B = A^power
+    bool start_given = false; // u already holds the start vector (packed FP64)
+    bool single = false;      // one expansion only: H of the k-step Arnoldi in Hsingle
+    Mat Hsingle;
 
     Solver(ovl_lattice L, double mu_, double m_w, int p_, int nev_)
         : lat(L), st(L->stream), N(L->N), p(p_), nev(nev_), mu(mu_), kappa(1.0 / (8.0 + 2.0 * m_w)), mem{L} {}
@@ -155,7 +159,7 @@ class Solver {
         return OVL_OK;
     }
 
-    // w = B u = A (A u)
+    // w = B u = A (A u), or A u when power == 1
     int apply_B() {
         DslashArgs a;
         a.in = (const void* const*)dsl;
@@ -163,6 +167,11 @@ class Solver {
         a.mu = d_mu;
         a.nrhs = 1;
         a.kappa = kappa;
+        if (power == 1) {
+            a.out = (void* const*)(dsl + 3);  // straight into w
+            matvecs++;
+            return ovl_dslash_launch(lat, a, OVL_VEC_F64, OVL_LINKS_F64, st);
+        }
         if (int rc = ovl_dslash_launch(lat, a, OVL_VEC_F64, OVL_LINKS_F64, st)) return rc;
         a.in = (const void* const*)(dsl + 2);
         a.out = (void* const*)(dsl + 3);
@@ -233,10 +242,11 @@ class Solver {
     }
 
     int run(double tol, int max_restarts, uint64_t seed) {
-        if (int rc = alloc()) return rc;
+        if (!Va_hi)
+            if (int rc = alloc()) return rc;
         const size_t ld = p + 1;
         // random start vector (seeded), packed order is irrelevant for it
-        {
+        if (!start_given) {
             std::mt19937_64 gen(seed);
             std::normal_distribution<double> nd;
             std::vector<double2> x(N);
@@ -338,6 +348,10 @@ class Solver {
             Mat Hp(pc, pc);
             for (int j = 0; j < pc; j++)
                 for (int i = 0; i < pc; i++) Hp(i, j) = cd(Hh2[i + j * ld].x, Hh2[i + j * ld].y);
+            if (single) {
+                Hsingle = Hp;
+                return OVL_OK;
+            }
             // residual norm beta = |u| after the correction
             Mat nn;
             std::vector<double2*> xs{u};
@@ -662,5 +676,76 @@ extern "C" int ovl_deflation_setup(ovl_lattice lat, double mu, double m_w, int s
         return rc;
     }
     *out = d;
+    return OVL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// features of the (k, m) predictor
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_link_spread(const double2* __restrict__ u64, size_t V, double* __restrict__ part) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 4 * V; i += (size_t)gridDim.x * blockDim.x) {
+        size_t nu = i / V, site = i - nu * V;
+        double tr = u64[(nu * 9 + 0) * V + site].x + u64[(nu * 9 + 4) * V + site].x + u64[(nu * 9 + 8) * V + site].x;
+        acc += 1.0 - tr / 3.0;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+}  // namespace
+
+extern "C" int ovl_link_spread(ovl_lattice lat, double* spread) {
+    if (!lat || !spread) return ovl_fail(lat, OVL_EINVAL, "ovl_link_spread: null argument");
+    if (!lat->have_links) return ovl_fail(lat, OVL_EINVAL, "ovl_link_spread: links not set");
+    const int nb = 256;
+    void* s;
+    if (int rc = ovl_scratch(lat, nb * sizeof(double), &s)) return rc;
+    k_link_spread<<<nb, 256, 0, lat->stream>>>(lat->links.u64, lat->V, (double*)s);
+    OVL_LAUNCH_CHECK(lat);
+    std::vector<double> h(nb);
+    OVL_CUDA_TRY(lat, cudaMemcpyAsync(h.data(), s, nb * sizeof(double), cudaMemcpyDeviceToHost, lat->stream));
+    OVL_CUDA_TRY(lat, cudaStreamSynchronize(lat->stream));
+    double t = 0.0;
+    for (double v : h) t += v;
+    *spread = t / (4.0 * (double)lat->V);
+    return OVL_OK;
+}
+
+extern "C" int ovl_ritz_values(ovl_lattice lat, double mu, double m_w, int k, const double* b, double* out) {
+    if (!lat || !b || !out) return ovl_fail(lat, OVL_EINVAL, "ovl_ritz_values: null argument");
+    if (!lat->have_links) return ovl_fail(lat, OVL_EINVAL, "ovl_ritz_values: links not set");
+    if (k < 1 || (size_t)k + 2 > lat->N || k > OVL_MAXCOL - 2)
+        return ovl_fail(lat, OVL_EINVAL, "ovl_ritz_values: k=%d out of range", k);
+    Solver sv(lat, mu, m_w, k, 1);
+    sv.power = 1;
+    sv.single = true;
+    if (int rc = sv.alloc()) return rc;
+    // b (canonical, host or device) -> packed FP64 in u
+    size_t cb = lat->N * sizeof(double2);
+    const double* src = b;
+    void* s;
+    if (int rc = ovl_scratch(lat, cb, &s)) return rc;
+    if (!ovl_is_device_ptr(b)) {
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(s, b, cb, cudaMemcpyHostToDevice, lat->stream));
+        src = (const double*)s;
+    }
+    if (int rc = ovl_pack_impl(lat, src, sv.u, 1, OVL_VEC_F64, lat->stream)) return rc;
+    sv.start_given = true;
+    if (int rc = sv.run(1e-12, 0, 0)) return rc;
+    Mat T, Z;
+    if (!sla::schur(sv.Hsingle, T, Z)) return ovl_fail(lat, OVL_ENOCONV, "ovl_ritz_values: small Schur failed");
+    int n = T.r;
+    for (int i = 0; i < k; i++) {
+        cd v = i < n ? T(i, i) : cd(0.0);
+        out[2 * i] = v.real();
+        out[2 * i + 1] = v.imag();
+    }
     return OVL_OK;
 }

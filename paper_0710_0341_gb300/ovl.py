@@ -58,6 +58,17 @@ _SIGS = {
     "ovl_sign_apply": (C.c_int, [_P, C.c_int, C.POINTER(ovl_sign_params), C.POINTER(_P), _P, _P,
                                  C.POINTER(ovl_sign_info)]),
     "ovl_launch_count": (C.c_int, [_P, C.POINTER(C.c_longlong)]),
+    "ovl_mlp_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(_P)]),
+    "ovl_mlp_destroy": (C.c_int, [_P]),
+    "ovl_mlp_num_params": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "ovl_mlp_set_params": (C.c_int, [_P, _P]),
+    "ovl_mlp_get_params": (C.c_int, [_P, _P]),
+    "ovl_mlp_forward": (C.c_int, [_P, _P, C.c_int, _P]),
+    "ovl_mlp_loss_grad": (C.c_int, [_P, _P, _P, C.c_int, C.c_float, _P, _P]),
+    "ovl_mlp_train": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_float, C.c_float, _P]),
+    "ovl_mlp_last_error": (C.c_char_p, [_P]),
+    "ovl_link_spread": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "ovl_ritz_values": (C.c_int, [_P, C.c_double, C.c_double, C.c_int, _P, _P]),
     "ovl_profile": (C.c_int, [_P, C.c_int, _P]),
     "ovl_last_error": (C.c_char_p, [_P]),
     "ovl_version": (C.c_char_p, []),
@@ -229,6 +240,67 @@ def ovl_profile(h, enable):
     _check(lib().ovl_profile(h, int(enable), C.cast(buf, _P)), h)
     return {n: dict(launches=int(buf[3 * i]), ms=buf[3 * i + 1], bytes=buf[3 * i + 2])
             for i, n in enumerate(PROF_CLASSES)}
+
+
+def _mcheck(rc, net=None):
+    if rc != OVL_OK:
+        m = lib().ovl_last_error(None)
+        raise OvlError(rc, m.decode() if m else "")
+
+
+def ovl_mlp_create(n_in, n_hidden, n_out):
+    net = _P()
+    _mcheck(lib().ovl_mlp_create(int(n_in), int(n_hidden), int(n_out), C.byref(net)))
+    return net
+
+
+def ovl_mlp_destroy(net):
+    _mcheck(lib().ovl_mlp_destroy(net))
+
+
+def ovl_mlp_num_params(net):
+    n = C.c_int()
+    _mcheck(lib().ovl_mlp_num_params(net, C.byref(n)))
+    return n.value
+
+
+def ovl_mlp_set_params(net, theta):
+    _mcheck(lib().ovl_mlp_set_params(net, _ptr(theta)))
+
+
+def ovl_mlp_get_params(net, theta):
+    _mcheck(lib().ovl_mlp_get_params(net, _ptr(theta)))
+    return theta
+
+
+def ovl_mlp_forward(net, X, Y):
+    _mcheck(lib().ovl_mlp_forward(net, _ptr(X), int(X.shape[0]), _ptr(Y)))
+    return Y
+
+
+def ovl_mlp_loss_grad(net, X, T, under_weight, grad):
+    loss = (C.c_float * 1)()
+    _mcheck(lib().ovl_mlp_loss_grad(net, _ptr(X), _ptr(T), int(X.shape[0]), float(under_weight),
+                                    C.cast(loss, _P), _ptr(grad)))
+    return float(loss[0])
+
+
+def ovl_mlp_train(net, X, T, steps, lr, under_weight):
+    loss = (C.c_float * 1)()
+    _mcheck(lib().ovl_mlp_train(net, _ptr(X), _ptr(T), int(X.shape[0]), int(steps), float(lr), float(under_weight),
+                                C.cast(loss, _P)))
+    return float(loss[0])
+
+
+def ovl_link_spread(h):
+    v = C.c_double()
+    _check(lib().ovl_link_spread(h, C.byref(v)), h)
+    return v.value
+
+
+def ovl_ritz_values(h, mu, m_w, k, b, out):
+    _check(lib().ovl_ritz_values(h, float(mu), float(m_w), int(k), _ptr(b), _ptr(out)), h)
+    return out
 
 
 def ovl_last_error(h=None):

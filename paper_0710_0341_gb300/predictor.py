@@ -1,0 +1,163 @@
+"""Learned (k, m) predictor: features, training data from the method's own runs,
+GPU training and prediction (not in the paper).
+
+The network (libovl's MLP: 20 -> 64 -> 64 -> 2, FP32, own forward/backward/Adam
+kernels) maps solve features to (log k, log(m + 1)):
+
+  features = [mu, m_w, link spread, log2 V, the 16 smallest |Re theta| of the
+              64 Ritz values from a 64-step Arnoldi run on the source]
+
+Labels are the cost-minimal (k, m) over a grid of deflation sizes: for each m
+the GPU computes the deflation data (ovl_deflation_setup, Schur) and runs the
+adaptive depth to the target accuracy; the cost in basis-vector passes is
+  k (k/2 + m) + setup_passes(m) / sources
+with setup_passes = (A^2 applications) x (basis size), shared by `sources`
+solves of the same operator. This module only sequences library calls and
+moves arrays; every computation runs in libovl.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+from paper_0710_0341_gb300 import ovl, synth
+
+N_IN, N_HIDDEN, N_OUT = 20, 64, 2
+M_GRID = (0, 8, 16, 24)
+NRITZ, NFEAT_RITZ = 64, 16
+UNDER_WEIGHT = 4.0
+HERE = os.path.dirname(os.path.abspath(__file__))
+DATA = os.path.join(HERE, "predictor_data.json")
+
+
+def features(h, dims, mu, m_w, b):
+    V = int(np.prod(dims))
+    spread = ovl.ovl_link_spread(h)
+    th = np.zeros(NRITZ, dtype=np.complex128)
+    ovl.ovl_ritz_values(h, mu, m_w, NRITZ, np.ascontiguousarray(b), th)
+    re = np.sort(np.abs(th.real))[:NFEAT_RITZ]
+    return np.concatenate([[mu, m_w, spread, math.log2(V)], re]).astype(np.float32)
+
+
+def setup_passes(matvecs, m):
+    nev = m + max(8, m // 2)
+    return matvecs * max(4 * nev, nev + 60)
+
+
+def measure(h, mu, m_w, b, tol=1e-8, k0=20, every=10, k_max=600, sources=12):
+    """For each m of M_GRID: the adaptive depth that reaches tol and its cost."""
+    defl, setup = [None], [0.0]
+    for m in M_GRID[1:]:
+        d = ovl.ovl_deflation_setup(h, mu, m_w, ovl.OVL_DEFL_SCHUR, m, 1e-12, 3000)
+        defl.append(d)
+        setup.append(setup_passes(ovl.ovl_deflation_stats(d)[1], m) / sources)
+    n = len(M_GRID)
+    bb = np.stack([b] * n)
+    y = np.zeros_like(bb)
+    ps = [dict(mu=mu, m_w=m_w, k=k0, adapt_every=every, k_max=k_max, tol=tol)] * n
+    try:
+        infos = ovl.ovl_sign_apply(h, ps, defl, bb, y)
+    except ovl.OvlError as e:  # keep the solves that finished
+        infos = e.infos
+    out = []
+    for m, inf, sc in zip(M_GRID, infos, setup):
+        k = inf["k_used"]
+        ok = inf["status"] == 0 and inf["err_est"] <= tol / 10 and k < k_max
+        out.append(dict(m=m, k=k, ok=bool(ok), cost=k * (k / 2 + m) + sc, err_est=inf["err_est"]))
+    for d in defl[1:]:
+        ovl.ovl_destroy_deflation(d)
+    return out
+
+
+def random_config(rng):
+    return dict(eps=float(rng.uniform(0.2, 0.6)), mu=float(rng.uniform(0.0, 0.6)),
+                m_w=float(rng.uniform(-1.5, -0.8)), seed=int(rng.integers(1 << 30)))
+
+
+def run_config(cfg, dims=(4, 4, 4, 4)):
+    U = synth.random_su3_field(dims, cfg["eps"], cfg["seed"])
+    b = synth.gaussian_source(dims, cfg["seed"] + 1)
+    h = ovl.ovl_create_lattice(dims)
+    try:
+        ovl.ovl_set_links(h, U)
+        f = features(h, dims, cfg["mu"], cfg["m_w"], b)
+        res = measure(h, cfg["mu"], cfg["m_w"], b)
+    finally:
+        ovl.ovl_destroy_lattice(h)
+    good = [r for r in res if r["ok"]]
+    best = min(good, key=lambda r: r["cost"]) if good else None
+    return dict(config=cfg, features=[float(v) for v in f], results=res,
+                label=None if best is None else [best["k"], best["m"]])
+
+
+def generate(n, seed=0, path=DATA):
+    rng = np.random.default_rng(seed)
+    rows = []
+    t0 = time.time()
+    for i in range(n):
+        rows.append(run_config(random_config(rng)))
+        print(f"[{i + 1}/{n}] {time.time() - t0:.0f}s label {rows[-1]['label']}", flush=True)
+    json.dump({"dims": [4, 4, 4, 4], "m_grid": list(M_GRID), "rows": rows}, open(path, "w"))
+    return rows
+
+
+def to_xy(rows):
+    rows = [r for r in rows if r["label"] is not None]
+    X = np.array([r["features"] for r in rows], dtype=np.float32)
+    T = np.array([[math.log(r["label"][0]), math.log(r["label"][1] + 1)] for r in rows], dtype=np.float32)
+    return X, T
+
+
+class Predictor:
+    """Standardised features -> MLP (GPU) -> (k, m)."""
+
+    def __init__(self, seed=0):
+        self.net = ovl.ovl_mlp_create(N_IN, N_HIDDEN, N_OUT)
+        npar = ovl.ovl_mlp_num_params(self.net)
+        rng = np.random.default_rng(seed)
+        # He initialisation drawn on the host (input data), biases zero
+        theta = []
+        for fan_in, fan_out in ((N_IN, N_HIDDEN), (N_HIDDEN, N_HIDDEN), (N_HIDDEN, N_OUT)):
+            theta.append(rng.standard_normal(fan_in * fan_out) * math.sqrt(2.0 / fan_in))
+            theta.append(np.zeros(fan_out))
+        self.theta0 = np.concatenate(theta).astype(np.float32)
+        assert self.theta0.size == npar
+        ovl.ovl_mlp_set_params(self.net, self.theta0)
+        self.mu_x = np.zeros(N_IN, np.float32)
+        self.sd_x = np.ones(N_IN, np.float32)
+
+    def fit(self, X, T, steps=3000, lr=3e-3):
+        self.mu_x = X.mean(0)
+        self.sd_x = X.std(0) + 1e-6
+        Xs = ((X - self.mu_x) / self.sd_x).astype(np.float32)
+        return ovl.ovl_mlp_train(self.net, np.ascontiguousarray(Xs), np.ascontiguousarray(T), steps, lr,
+                                 UNDER_WEIGHT)
+
+    def predict(self, X):
+        Xs = ((np.atleast_2d(X) - self.mu_x) / self.sd_x).astype(np.float32)
+        Y = np.zeros((Xs.shape[0], N_OUT), np.float32)
+        ovl.ovl_mlp_forward(self.net, np.ascontiguousarray(Xs), Y)
+        k = np.exp(Y[:, 0])
+        m = np.exp(Y[:, 1]) - 1
+        return k, m
+
+    def close(self):
+        ovl.ovl_mlp_destroy(self.net)
+
+
+def nearest_m(m):
+    return min(M_GRID, key=lambda g: abs(g - m))
+
+
+if __name__ == "__main__":
+    import sys
+
+    from paper_0710_0341_gb300 import build
+
+    build.build()
+    n = int(sys.argv[1]) if len(sys.argv) > 1 else 48
+    generate(n, path=sys.argv[2] if len(sys.argv) > 2 else DATA)
