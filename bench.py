@@ -233,14 +233,9 @@ def main():
     launches = (ovl.ovl_launch_count(h) - n0) // args.steps
     clocks = clk.stop()
     ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
     nsolve = len(params)
-    value = ws * nsolve * args.steps / (ms / 1e3)
+    ms, value = replica_throughput(ms, nsolve * args.steps, ws, "cuda")
+    torch.cuda.synchronize()
     # ---- end to end through the C ABI with host buffers ----
     yh = np.zeros_like(b)
     step_e2e = lambda: ovl.ovl_sign_apply(h, params, defl, b, yh)  # noqa: E731
@@ -292,6 +287,22 @@ def main():
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def replica_throughput(ms_local, units_local, ws, device):
+    """Replicas: every rank does the same work on its own GPU; the job time is
+    the slowest rank's, the value all ranks' units over that time."""
+    import torch
+
+    ms = ms_local
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    return ms, ws * units_local / (ms / 1e3)
 
 
 def stencil_gbs(torch, ovl, synth):

@@ -224,6 +224,12 @@ int ovl_ritz_values(ovl_lattice lat, double mu, double m_w, int k, const double*
 int ovl_launch_count(ovl_lattice lat, long long* n);
 int ovl_profile(ovl_lattice lat, int enable, double* stats);
 
+/* Failure-detection self test: one CTA waits at a two-member device barrier
+ * that nobody else joins, with the same bounded wait the Newton kernel uses
+ * (max_polls polls of about 100 ns, at most 2^24). *status receives
+ * OVL_ETIMEOUT when the wait gave up as designed; the context stays usable. */
+int ovl_wait_selftest(ovl_lattice lat, long long max_polls, int* status);
+
 /* Message for the last failed call on this handle (NULL handle: the last
  * failure of a call that had no handle yet, e.g. ovl_create_lattice). */
 const char* ovl_last_error(ovl_lattice lat);

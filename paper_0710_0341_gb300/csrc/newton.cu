@@ -14,6 +14,7 @@
 // Barriers are counters in global memory with a bounded wait: a wait that
 // runs out sets OVL_ETIMEOUT for the solve and every CTA of the group leaves.
 #include "newton.cuh"
+#include "wait.cuh"
 
 namespace {
 
@@ -25,37 +26,9 @@ struct Group {
     int s, g, cpm;
 };
 
-// Barrier for the CTAs of one solve. Returns false if it timed out here or
-// anywhere else in the group.
-__device__ bool group_sync(NewtonDev& d, unsigned& gen, int cpm) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        gen++;
-        unsigned target = gen * (unsigned)cpm;
-        __threadfence();
-        atomicAdd(d.bar, 1u);
-        long long it = 0;
-        int good = 1;
-        while (true) {
-            unsigned v = *((volatile unsigned*)d.bar);
-            if (v >= target) break;
-            if (*((volatile int*)d.status) == OVL_ETIMEOUT) {
-                good = 0;
-                break;
-            }
-            if (++it > SPIN_LIMIT) {
-                atomicExch(d.status, OVL_ETIMEOUT);
-                good = 0;
-                break;
-            }
-            __nanosleep(64);
-        }
-        __threadfence();
-        ok = good;
-    }
-    __syncthreads();
-    return ok != 0;
+// Barrier for the CTAs of one solve (group_wait in wait.cuh, bounded).
+__device__ __forceinline__ bool group_sync(NewtonDev& d, unsigned& gen, int cpm) {
+    return group_wait(d.bar, d.status, gen, cpm, SPIN_LIMIT);
 }
 
 __device__ __forceinline__ double warp_maxloc(double v, int& idx) {

@@ -68,6 +68,7 @@ _SIGS = {
     "ovl_mlp_train": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_float, C.c_float, _P]),
     "ovl_mlp_last_error": (C.c_char_p, [_P]),
     "ovl_link_spread": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "ovl_wait_selftest": (C.c_int, [_P, C.c_longlong, C.POINTER(C.c_int)]),
     "ovl_ritz_values": (C.c_int, [_P, C.c_double, C.c_double, C.c_int, _P, _P]),
     "ovl_profile": (C.c_int, [_P, C.c_int, _P]),
     "ovl_last_error": (C.c_char_p, [_P]),
@@ -290,6 +291,12 @@ def ovl_mlp_train(net, X, T, steps, lr, under_weight):
     _mcheck(lib().ovl_mlp_train(net, _ptr(X), _ptr(T), int(X.shape[0]), int(steps), float(lr), float(under_weight),
                                 C.cast(loss, _P)))
     return float(loss[0])
+
+
+def ovl_wait_selftest(h, max_polls=10000):
+    st = C.c_int()
+    _check(lib().ovl_wait_selftest(h, int(max_polls), C.byref(st)), h)
+    return st.value
 
 
 def ovl_link_spread(h):

@@ -50,12 +50,17 @@ def setup_passes(matvecs, m):
 
 def measure(h, mu, m_w, b, tol=1e-8, k0=20, every=10, k_max=600, sources=12):
     """For each m of M_GRID: the adaptive depth that reaches tol and its cost."""
-    defl, setup = [None], [0.0]
+    grid, defl, setup, failed = [0], [None], [0.0], []
     for m in M_GRID[1:]:
-        d = ovl.ovl_deflation_setup(h, mu, m_w, ovl.OVL_DEFL_SCHUR, m, 1e-12, 3000)
+        try:
+            d = ovl.ovl_deflation_setup(h, mu, m_w, ovl.OVL_DEFL_SCHUR, m, 1e-12, 800)
+        except ovl.OvlError:  # eigensolver did not converge: this m is not an option
+            failed.append(m)
+            continue
+        grid.append(m)
         defl.append(d)
         setup.append(setup_passes(ovl.ovl_deflation_stats(d)[1], m) / sources)
-    n = len(M_GRID)
+    n = len(grid)
     bb = np.stack([b] * n)
     y = np.zeros_like(bb)
     ps = [dict(mu=mu, m_w=m_w, k=k0, adapt_every=every, k_max=k_max, tol=tol)] * n
@@ -64,10 +69,13 @@ def measure(h, mu, m_w, b, tol=1e-8, k0=20, every=10, k_max=600, sources=12):
     except ovl.OvlError as e:  # keep the solves that finished
         infos = e.infos
     out = []
-    for m, inf, sc in zip(M_GRID, infos, setup):
+    for m, inf, sc in zip(grid, infos, setup):
         k = inf["k_used"]
         ok = inf["status"] == 0 and inf["err_est"] <= tol / 10 and k < k_max
         out.append(dict(m=m, k=k, ok=bool(ok), cost=k * (k / 2 + m) + sc, err_est=inf["err_est"]))
+    for m in failed:
+        out.append(dict(m=m, k=k_max, ok=False, cost=float("inf"), err_est=None))
+    out.sort(key=lambda r: r["m"])
     for d in defl[1:]:
         ovl.ovl_destroy_deflation(d)
     return out
@@ -101,7 +109,7 @@ def generate(n, seed=0, path=DATA):
     for i in range(n):
         rows.append(run_config(random_config(rng)))
         print(f"[{i + 1}/{n}] {time.time() - t0:.0f}s label {rows[-1]['label']}", flush=True)
-    json.dump({"dims": [4, 4, 4, 4], "m_grid": list(M_GRID), "rows": rows}, open(path, "w"))
+        json.dump({"dims": [4, 4, 4, 4], "m_grid": list(M_GRID), "rows": rows}, open(path, "w"))
     return rows
 
 
