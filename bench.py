@@ -35,6 +35,10 @@ EPS, SEED, MW = 0.4, 0, -1.0
 MUS = [0.0, 0.1, 0.3, 0.6]
 K_KRYLOV, M_DEFL = 400, 30
 METRIC = "sgn(H_w(mu)) b solves/s at 1e-8 rel err vs FP64 oracle"
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
+# over the launches of one timed step) from the ncu launch list of this
+# command, profiles/bench_launches_8x4.md; valid while the kernel is unchanged.
+NCU_TRAFFIC = {"gs_pass_b": 1.3724e9, "gs_pass_a": 0.6880e9}
 WORKLOAD = "8^4 eps=0.4 m_w=-1 mu={0,0.1,0.3,0.6} x {Schur,LR} k=400 m=30, FP64 mode"
 
 
@@ -255,7 +259,9 @@ def main():
     pd = prof[dom]
     achieved = (pd["bytes"] / pd["launches"]) / (pd["ms"] / pd["launches"] / 1e3) / 1e9 if pd["launches"] else None
     roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm if achieved else None, "traffic": None,
+            "frac": achieved / hbm if achieved else None, "traffic": NCU_TRAFFIC.get(dom),
+            "traffic_unit": "bytes per launch (ncu)", "algorithmic_bytes_per_launch":
+                pd["bytes"] / pd["launches"] if pd["launches"] else None,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback 6800 GB/s"}
     breakdown = {c: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                      "GB_per_s": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 and v["bytes"] > 0 else None}
