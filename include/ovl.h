@@ -72,7 +72,10 @@ typedef struct {
     int    prec;        /* OVL_PREC_* */
     int    newton_max_iter;  /* <= 0: default 100 */
     double newton_tol;       /* <= 0: default 1e-13 (relative Frobenius step) */
-    int    newton_fp64;      /* 0: double-float Gauss-Jordan (default); 1: FP64 Gauss-Jordan */
+    int    newton_fp64;      /* 0: double-float Gauss-Jordan (default: one thread-block cluster
+                              * per matrix when its rows fit the cluster's shared memory, else
+                              * the cooperative kernel); 1: FP64 Gauss-Jordan; 2: double-float,
+                              * always the cooperative kernel */
     /* Adaptive Krylov depth (not in the paper): with adapt_every = d > 0 the
      * solve starts checking at depth k and then every d steps up to k_max:
      * the estimate est_j = |g_j - (g_{j-d}; 0)| / |g_j| compares the

@@ -23,8 +23,6 @@
 namespace {
 
 constexpr int DOT_THREADS = 256;
-constexpr int DOT_RPL = 8;                      // rows per lane (4 float4 = 8 complex)
-constexpr int DOT_RB = 32 * DOT_RPL;            // rows per block iteration
 constexpr int UPD_RPL = 4;
 constexpr int UPD_RB = 32 * UPD_RPL;
 
@@ -48,7 +46,7 @@ __device__ __forceinline__ bool solve_in_step(const SolveDev& d, int j) {
 // ---------------------------------------------------------------------------
 // pass A: a = Q_p^dag u, b = Q_p^dag w and the scalars |u|^2, u^dag w, |w|^2
 //
-// A CTA takes a block of DOT_RB rows (u and w staged in shared memory as
+// A CTA takes a block of DOTB_RB rows (u and w staged in shared memory as
 // FP32) and a group of columns (c = cg + CG * (warp + 8 i)); a warp streams one
 // column at a time, each lane reading 16 float4 (32 rows) of it, and reduces
 // across lanes once per column and row block. Row blocks are visited in a
@@ -187,10 +185,16 @@ __global__ void __launch_bounds__(256) k_gs_reduce(BatchDev B, int j, int G_used
 // small step: d = H a (FP32 is enough: |a| is at the rounding level of one
 // Gram-Schmidt pass), then nu, c, e and the pass-B coefficients; H update.
 // j < 0: final pass after the last step (only the H update of column p-1).
+//
+// Phase 1 tiles H into 32-row x 64-column blocks (a warp takes 8 columns,
+// a lane one row: 8 independent loads per thread); each tile writes one
+// partial per row, and the last tile of a solve to finish sums the partials
+// in column-tile order (deterministic) and runs phase 2.
 // ---------------------------------------------------------------------------
-constexpr int SM_ROWS = 64;
+constexpr int SM_TR = 32;  // rows per tile
+constexpr int SM_TC = 64;  // columns per tile (8 per warp)
 
-__global__ void __launch_bounds__(256) k_gs_small(BatchDev B, int j) {
+__global__ void __launch_bounds__(256) k_gs_small(BatchDev B, int j, int ctmax) {
     const int s = blockIdx.y;
     SolveDev& d = B.sd[s];
     if (!solve_in_step(d, j)) return;
@@ -198,37 +202,51 @@ __global__ void __launch_bounds__(256) k_gs_small(BatchDev B, int j) {
     const int ld = d.ldH;
     const bool first = (j == 1);
     const bool final_pass = (j < 0);
-    __shared__ float2 a32[OVL_MAXCOL];
-    __shared__ float2 red[4][SM_ROWS];
+    __shared__ float2 red[8][SM_TR];
     __shared__ int is_last;
     const int tid = threadIdx.x;
     const double2* dots = d.dots;
     // phase 1: rows of d (not needed for the first step or the final pass)
     if (!first && !final_pass) {
-        for (int c = tid; c < p; c += 256) a32[c] = make_float2((float)dots[c].x, (float)dots[c].y);
-        __syncthreads();
-        const int row = blockIdx.x * SM_ROWS + (tid & (SM_ROWS - 1));
-        const int cg = tid / SM_ROWS;  // 0..3
+        if (d.dpart == nullptr) {  // descriptor without partial buffer: refuse, do not write
+            if (blockIdx.x == 0 && tid == 0) {
+                d.status = OVL_EINVAL;
+                d.active = 0;
+            }
+            return;
+        }
+        const int lane = tid & 31, warp = tid >> 5;
+        const int tr = blockIdx.x / ctmax, tc = blockIdx.x % ctmax;
+        const int row = tr * SM_TR + lane;
+        const int cb = tc * SM_TC + warp * 8;
+        // H is upper Hessenberg below the Schur block: row i has no entries left of column i-1
+        const int cmin = row >= d.m_q + 1 ? row - 1 : 0;
         float2 acc = make_float2(0.f, 0.f);
-        if (row < p) {
-            // H is upper Hessenberg below the Schur block: row i has no entries left of column i-1
-            int c0 = row >= d.m_q + 1 ? row - 1 : 0;
-            for (int c = c0 + cg; c < p; c += 4) {
-                float2 h = d.H32[row + (size_t)c * ld];
-                float2 av = a32[c];
-                acc.x = fmaf(h.x, av.x, fmaf(-h.y, av.y, acc.x));
-                acc.y = fmaf(h.x, av.y, fmaf(h.y, av.x, acc.y));
+        if (row < p && tc * SM_TC < p) {
+            float2 h[8], av[8];
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                const int c = cb + t;
+                const bool on = c < p && c >= cmin;
+                h[t] = on ? d.H32[row + (size_t)c * ld] : make_float2(0.f, 0.f);
+                const double2 a = c < p ? dots[c] : make_double2(0.0, 0.0);
+                av[t] = make_float2((float)a.x, (float)a.y);
+            }
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                acc.x = fmaf(h[t].x, av[t].x, fmaf(-h[t].y, av[t].y, acc.x));
+                acc.y = fmaf(h[t].x, av[t].y, fmaf(h[t].y, av[t].x, acc.y));
             }
         }
-        red[cg][tid & (SM_ROWS - 1)] = acc;
+        red[warp][lane] = acc;
         __syncthreads();
-        if (tid < SM_ROWS && row < p) {
-            float2 t = red[0][tid];
-            for (int k = 1; k < 4; k++) {
-                t.x += red[k][tid].x;
-                t.y += red[k][tid].y;
+        if (warp == 0 && row < p && tc * SM_TC < p) {
+            float2 t = red[0][lane];
+            for (int k = 1; k < 8; k++) {
+                t.x += red[k][lane].x;
+                t.y += red[k][lane].y;
             }
-            d.dvec[row] = make_double2(t.x, t.y);
+            d.dpart[(size_t)tc * ld + row] = t;
         }
         __threadfence();
         __syncthreads();
@@ -236,6 +254,17 @@ __global__ void __launch_bounds__(256) k_gs_small(BatchDev B, int j) {
         __syncthreads();
         if (!is_last) return;
         __threadfence();
+        const int nct = (p + SM_TC - 1) / SM_TC;
+        for (int r = tid; r < p; r += 256) {
+            float2 t = make_float2(0.f, 0.f);
+            for (int c = 0; c < nct; c++) {
+                const float2 v = __ldcg(d.dpart + (size_t)c * ld + r);
+                t.x += v.x;
+                t.y += v.y;
+            }
+            d.dvec[r] = make_double2(t.x, t.y);
+        }
+        __syncthreads();
     } else if (blockIdx.x != 0) {
         return;
     }
@@ -497,48 +526,65 @@ __global__ void __launch_bounds__(256) k_gs_update(BatchDev B, int j) {
 }
 
 // ---------------------------------------------------------------------------
-// accurate projections (FP64) for deflation and start vectors
+// accurate projections for deflation, start vectors and the final Galerkin
+// pass: P[c] = Q[:,c]^dag x in double-float (products of the 48-bit basis
+// hi + lo with x split into hi + lo, error about 2^-46 of sum |q| |x|), and
+// |x|^2 in FP64. Like pass A, a CTA stages a block of PJ_RB rows of x in
+// shared memory (split once) and a warp streams one column over the block,
+// each lane 32 rows, with one FP64 reduction per column and block.
 // ---------------------------------------------------------------------------
-constexpr int PJ_RPL = 4;
-constexpr int PJ_RB = 32 * PJ_RPL;
+constexpr int PJ_RB = 1024;
+constexpr int PJ_FL = PJ_RB / 64;  // float4 (two rows) per lane per column
 
 __global__ void __launch_bounds__(256) k_proj_dot(ProjDev* pds, double2* part, int G, int pstride, size_t N) {
     const int s = blockIdx.y;
     const ProjDev d = pds[s];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __shared__ double2 acc[OVL_MAXCOL + 1];
+    __shared__ float4 s_x[PJ_RB];  // x split: (hi.re, hi.im, lo.re, lo.im)
     for (int o = tid; o <= d.ncol; o += 256) acc[o] = make_double2(0.0, 0.0);
-    __syncthreads();
     for (size_t base = (size_t)blockIdx.x * PJ_RB; base < N; base += (size_t)gridDim.x * PJ_RB) {
-        double2 xv[PJ_RPL];
-#pragma unroll
-        for (int i = 0; i < PJ_RPL; i++) {
-            size_t r = base + 32 * i + lane;
-            xv[i] = r < N ? d.x[r] : make_double2(0.0, 0.0);
+        __syncthreads();  // acc zeroed / s_x reuse
+        double nn = 0.0;
+        for (int rr = tid; rr < PJ_RB; rr += 256) {
+            const size_t r = base + rr;
+            const double2 x = r < N ? d.x[r] : make_double2(0.0, 0.0);
+            const float2 xr = split_d(x.x), xi = split_d(x.y);
+            s_x[rr] = make_float4(xr.x, xi.x, xr.y, xi.y);
+            nn += x.x * x.x + x.y * x.y;
         }
-        if (warp == 0) {
-            double nn = 0.0;
-#pragma unroll
-            for (int i = 0; i < PJ_RPL; i++) nn += xv[i].x * xv[i].x + xv[i].y * xv[i].y;
-            nn = warp_sumd(nn);
-            if (lane == 0) acc[d.ncol].x += nn;
-        }
+        nn = warp_sumd(nn);
+        if (lane == 0) atomicAdd(&acc[d.ncol].x, nn);
+        __syncthreads();
+        const bool full = base + PJ_RB <= N;  // N is even: a float4 never straddles the end
         for (int c = warp; c < d.ncol; c += 8) {
-            const float2* qh = d.qhi[c];
-            const float2* ql = d.qlo ? d.qlo[c] : nullptr;  // no low plane: FP32 column
-            double ar = 0.0, ai = 0.0;
+            const float4* __restrict__ qh = (const float4*)d.qhi[c] + (base >> 1);
+            const float4* __restrict__ ql = d.qlo ? (const float4*)d.qlo[c] + (base >> 1) : nullptr;
+            dfacc a;
+            dfacc_zero(a);
 #pragma unroll
-            for (int i = 0; i < PJ_RPL; i++) {
-                size_t r = base + 32 * i + lane;
-                if (r < N) {
-                    float2 h = qh[r], l = ql ? ql[r] : make_float2(0.f, 0.f);
-                    double qr = (double)h.x + (double)l.x, qi = (double)h.y + (double)l.y;
-                    ar += qr * xv[i].x + qi * xv[i].y;
-                    ai += qr * xv[i].y - qi * xv[i].x;
+            for (int hb = 0; hb < 2; hb++) {  // two batches of loads in flight
+                float4 hv[PJ_FL / 2], lv[PJ_FL / 2];
+#pragma unroll
+                for (int i = 0; i < PJ_FL / 2; i++) {
+                    const int rl = 64 * (hb * (PJ_FL / 2) + i) + 2 * lane;
+                    const bool on = full || base + rl < N;
+                    hv[i] = on ? __ldg(qh + (rl >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    lv[i] = on && ql ? __ldg(ql + (rl >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int i = 0; i < PJ_FL / 2; i++) {
+                    const int rl = 64 * (hb * (PJ_FL / 2) + i) + 2 * lane;
+                    const float4 x0 = s_x[rl], x1 = s_x[rl + 1];
+                    // conj(q) x for rows rl, rl+1
+                    dfacc_mac(a, make_float2(hv[i].x, -hv[i].y), make_float2(lv[i].x, -lv[i].y),
+                              make_float2(x0.x, x0.y), make_float2(x0.z, x0.w));
+                    dfacc_mac(a, make_float2(hv[i].z, -hv[i].w), make_float2(lv[i].z, -lv[i].w),
+                              make_float2(x1.x, x1.y), make_float2(x1.z, x1.w));
                 }
             }
-            ar = warp_sumd(ar);
-            ai = warp_sumd(ai);
+            const double2 v = dfacc_value(a);
+            const double ar = warp_sumd(v.x), ai = warp_sumd(v.y);
             if (lane == 0) {
                 acc[c].x += ar;
                 acc[c].y += ai;
@@ -664,8 +710,9 @@ int ovl_gs_grid(ovl_lattice lat) {
 }
 
 int ovl_gs_dot(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
-    // column groups: enough CTAs to cover every SM about twice
-    int cgs = (2 * lat->num_sms + b.G * b.nsolve - 1) / (b.G * b.nsolve);
+    // column groups: about eight CTAs per SM (measured: 3 % faster than two
+    // per SM at 8^4, 8 solves; u and w are re-staged per group from L2)
+    int cgs = (8 * lat->num_sms + b.G * b.nsolve - 1) / (b.G * b.nsolve);
     if (cgs < 1) cgs = 1;
     if (cgs > 8) cgs = 8;
     if (b.pmax < 8 * cgs) cgs = std::max(1, b.pmax / 8);
@@ -684,9 +731,10 @@ int ovl_gs_reduce(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
 }
 
 int ovl_gs_small(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
-    // enough blocks for the longest solve (p < OVL_MAXCOL)
-    dim3 grid(j == 1 || j < 0 ? 1 : (b.pmax + SM_ROWS - 1) / SM_ROWS, b.nsolve);
-    k_gs_small<<<grid, 256, 0, st>>>(b, j);
+    // tiles of the largest solve (p <= pmax < OVL_MAXCOL)
+    const int ctmax = (b.pmax + SM_TC - 1) / SM_TC, trmax = (b.pmax + SM_TR - 1) / SM_TR;
+    dim3 grid(j == 1 || j < 0 ? 1 : ctmax * trmax, b.nsolve);
+    k_gs_small<<<grid, 256, 0, st>>>(b, j, ctmax > 0 ? ctmax : 1);
     OVL_LAUNCH_CHECK(lat);
     return OVL_OK;
 }

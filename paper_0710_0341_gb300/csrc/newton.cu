@@ -581,3 +581,360 @@ int ovl_newton_df_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int nma
     lat->launches++;
     return OVL_OK;
 }
+
+// ===========================================================================
+// Cluster variant of the double-float Gauss-Jordan Newton. One thread-block
+// cluster (16 CTAs, one per SM of a GPC) inverts one matrix; the rows live
+// in the CTAs' shared memory (n^2 x 16 B fits 16 x 227 KB up to n of about
+// 470). Per pivot: every CTA picks its best unused row for the column and
+// copies it to a double-buffered candidate slot in its own shared memory,
+// the cluster meets at one hardware barrier, and every CTA reads the
+// candidates and then the winning row straight out of the owner's shared
+// memory (distributed shared memory). Clusters never wait on each other, so
+// the launch is not cooperative: more matrices than resident clusters simply
+// run in waves. All branches that skip a barrier (no work, singular pivot)
+// are taken by every CTA of a cluster alike, since they depend only on data
+// that every CTA reads identically, and each CTA passes one last barrier
+// before it exits, so no CTA leaves while another still reads its memory.
+// The scaling |det X|^(-1/n) accumulates |pivot|^2 as an FP32 mantissa and
+// an integer exponent (the scale factor needs no more than FP32 accuracy),
+// and the pivot reciprocal is formed in double-float, so the elimination
+// uses no FP64 instruction.
+// ===========================================================================
+#include <cooperative_groups.h>
+
+namespace {
+
+namespace cg = cooperative_groups;
+
+constexpr int NTC = 512;
+
+// 1 / z for a complex df value: conj(z) * (1 / |z|^2), the real reciprocal
+// refined by one Newton step in df (error about 2^-46 relative)
+__device__ __forceinline__ dfc dfc_inv(const dfc& z) {
+    float p1, e1, p2, e2, s, e;
+    two_prod(z.hi.x, z.hi.x, p1, e1);
+    two_prod(z.hi.y, z.hi.y, p2, e2);
+    two_sum(p1, p2, s, e);
+    float t = __fadd_rn(__fadd_rn(e, e1), e2);
+    t = fmaf(2.f * z.hi.x, z.lo.x, t);
+    t = fmaf(2.f * z.hi.y, z.lo.y, t);
+    df_norm(s, t);  // |z|^2 = s + t
+    const float r0 = __fdiv_rn(1.f, s);
+    float pr, pe;
+    two_prod(s, r0, pr, pe);
+    // residual 1 - (s + t) r0; 1 - pr is exact (pr is within an ulp of 1)
+    const float res = __fsub_rn(__fsub_rn(__fsub_rn(1.f, pr), pe), __fmul_rn(t, r0));
+    float rh, rl;
+    fast_two_sum(r0, __fmul_rn(r0, res), rh, rl);
+    const dfc zc = dfc_make(make_float2(z.hi.x, -z.hi.y), make_float2(z.lo.x, -z.lo.y));
+    return dfc_mul(zc, dfc_make(make_float2(rh, 0.f), make_float2(rl, 0.f)));
+}
+
+__global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve) {
+    extern __shared__ float4 csm[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int CL = (int)cl.num_blocks();
+    const int g = (int)cl.block_rank();
+    const int s = blockIdx.x / CL;
+    if (s >= nsolve) return;  // whole cluster
+    NewtonDev& d = nds[s];
+    if (!d.run) return;       // whole cluster
+    const int n = d.n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nr = (n - g + CL - 1) / CL;            // own rows: i = g + CL * r
+    const int nrmax = (n + CL - 1) / CL;
+    float4* X = (float4*)d.X;
+    float4* R = csm;                                 // nrmax x n
+    float4* crow = R + (size_t)nrmax * n;            // 2 x n candidate rows (read by the cluster)
+    float4* prow = crow + 2 * (size_t)n;             // n: scaled pivot row
+    float4* fcol = prow + n;                         // nrmax: column k of own rows
+    int* piv = (int*)(fcol + ((nrmax + 1) & ~1));
+    int* pinv = piv + n;
+    unsigned char* used = (unsigned char*)(pinv + n);
+    __shared__ float s_red[NTC / 32];
+    __shared__ int s_idx[NTC / 32];
+    __shared__ float c_val[2];                       // candidate |pivot|^2 (read by the cluster)
+    __shared__ int c_row[2];
+    __shared__ float c_part[2];                      // per-iteration partial sums (read by the cluster)
+    __shared__ int s_q, s_pr;
+    __shared__ float s_bv;
+    __shared__ float4 s_inv;
+    __shared__ float s_mant;
+    __shared__ int s_exp;
+    // X_0 = H (column-major FP64 input), own rows
+    for (int r = 0; r < nr; r++) {
+        const int i = g + CL * r;
+        for (int l = tid; l < n; l += NTC) X[(size_t)i * n + l] = dfc_pack(dfc_from(d.H[i + (size_t)l * d.ldH]));
+    }
+    bool scaling = true, converged = false, bad = false;
+    double prev_rel = 1e300;
+    int iter = 0;
+    __syncthreads();
+    while (iter < d.max_iter) {
+        iter++;
+        for (int r = 0; r < nr; r++) {
+            const int i = g + CL * r;
+            for (int l = tid; l < n; l += NTC) R[(size_t)r * n + l] = __ldcg(X + (size_t)i * n + l);
+        }
+        for (int i = tid; i < n; i += NTC) used[i] = 0;
+        if (tid == 0) {
+            s_mant = 1.f;
+            s_exp = 0;
+        }
+        __syncthreads();
+        for (int k = 0; k < n; k++) {
+            const int slot = k & 1;
+            float best = -1.f;
+            int br = -1;
+            for (int r = tid; r < nr; r += NTC) {
+                if (used[g + CL * r]) continue;
+                const float4 v = R[(size_t)r * n + k];
+                const float a = v.x * v.x + v.y * v.y;
+                if (a > best) {
+                    best = a;
+                    br = r;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, br, o);
+                if (ov > best || (ov == best && oi >= 0 && (br < 0 || oi < br))) {
+                    best = ov;
+                    br = oi;
+                }
+            }
+            if (lane == 0) {
+                s_red[warp] = best;
+                s_idx[warp] = br;
+            }
+            __syncthreads();
+            best = s_red[0];
+            br = s_idx[0];
+            for (int w = 1; w < NTC / 32; w++)
+                if (s_red[w] > best || (s_red[w] == best && s_idx[w] >= 0 && (br < 0 || s_idx[w] < br))) {
+                    best = s_red[w];
+                    br = s_idx[w];
+                }
+            if (br >= 0)
+                for (int l = tid; l < n; l += NTC) crow[(size_t)slot * n + l] = R[(size_t)br * n + l];
+            if (tid == 0) {
+                c_val[slot] = br >= 0 ? best : -1.f;
+                c_row[slot] = br >= 0 ? g + CL * br : 0x7fffffff;
+            }
+            cl.sync();
+            // winner over the cluster: largest |pivot|^2, then smallest row
+            if (warp == 0) {
+                float v = -1.f;
+                int rw = 0x7fffffff, q = -1;
+                if (lane < CL) {
+                    v = *cl.map_shared_rank(&c_val[slot], lane);
+                    rw = *cl.map_shared_rank(&c_row[slot], lane);
+                    q = lane;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+                    const int orw = __shfl_xor_sync(0xffffffffu, rw, o);
+                    const int oq = __shfl_xor_sync(0xffffffffu, q, o);
+                    if (ov > v || (ov == v && orw < rw)) {
+                        v = ov;
+                        rw = orw;
+                        q = oq;
+                    }
+                }
+                if (lane == 0) {
+                    s_bv = v;
+                    s_pr = rw;
+                    s_q = q;
+                }
+            }
+            __syncthreads();
+            if (!(s_bv > 0.f) || s_q < 0) {  // same decision in every CTA
+                bad = true;
+                break;
+            }
+            const int pr = s_pr;
+            const float4* pw = cl.map_shared_rank(crow + (size_t)slot * n, s_q);
+            if (tid == 0) {
+                const dfc pv = dfc_unpack(pw[k]);
+                s_inv = dfc_pack(dfc_inv(pv));
+                int e;
+                const float mnt = frexpf(s_mant * (pv.hi.x * pv.hi.x + pv.hi.y * pv.hi.y), &e);
+                s_mant = mnt;
+                s_exp += e;
+                used[pr] = 1;
+                piv[k] = pr;
+            }
+            for (int r = tid; r < nr; r += NTC) fcol[r] = R[(size_t)r * n + k];
+            __syncthreads();
+            const dfc inv = dfc_unpack(s_inv);
+            for (int l = tid; l < n; l += NTC) prow[l] = l == k ? s_inv : dfc_pack(dfc_mul(dfc_unpack(pw[l]), inv));
+            __syncthreads();
+            const int rp = (pr % CL == g) ? (pr - g) / CL : -1;  // own index of the pivot row
+            // every (own row, column) pair once, flattened over the CTA
+            int r = tid / n, l = tid - (tid / n) * n;
+            const int total = nr * n;
+            for (int e = tid; e < total; e += NTC) {
+                const dfc pl = dfc_unpack(prow[l]);
+                if (r == rp) {
+                    R[(size_t)r * n + l] = prow[l];
+                } else {
+                    const dfc f = dfc_unpack(fcol[r]);
+                    float4* x = R + (size_t)r * n + l;
+                    *x = dfc_pack(dfc_fms(l == k ? dfc_zero() : dfc_unpack(*x), f, pl));
+                }
+                l += NTC;
+                while (l >= n) {
+                    l -= n;
+                    r++;
+                }
+            }
+            __syncthreads();
+        }
+        if (bad) break;
+        for (int k = tid; k < n; k += NTC) pinv[piv[k]] = k;
+        __syncthreads();
+        const double logdet = 0.5 * (log((double)s_mant) + (double)s_exp * 0.69314718055994530942);
+        const double c = scaling ? exp(-logdet / n) : 1.0, ic = 1.0 / c;
+        // inverse: Xinv[pinv(q)][piv[j]] = St[q][j] for the own stored rows q;
+        // X_new row pinv(q) = (c X + Xinv / c) / 2, written by this CTA only
+        float dsum = 0.f, nsum = 0.f;
+        for (int r = 0; r < nr; r++) {
+            const int i = pinv[g + CL * r];
+            float4* xr = X + (size_t)i * n;
+            for (int j = tid; j < n; j += NTC) {
+                const int l = piv[j];
+                const dfc xo = dfc_unpack(__ldcg(xr + l));  // rows of X move between CTAs
+                const dfc a = dfc_unpack(R[(size_t)r * n + j]);
+                const dfc xn = dfc_axpby(0.5 * c, xo, 0.5 * ic, a);
+                const float dr = (xn.hi.x - xo.hi.x) + (xn.lo.x - xo.lo.x);
+                const float di = (xn.hi.y - xo.hi.y) + (xn.lo.y - xo.lo.y);
+                dsum += dr * dr + di * di;
+                nsum += xn.hi.x * xn.hi.x + xn.hi.y * xn.hi.y;
+                xr[l] = dfc_pack(xn);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+            nsum += __shfl_xor_sync(0xffffffffu, nsum, o);
+        }
+        if (lane == 0) {
+            s_red[warp] = dsum;
+            s_idx[warp] = __float_as_int(nsum);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float a = 0.f, b = 0.f;
+            for (int w = 0; w < NTC / 32; w++) {
+                a += s_red[w];
+                b += __int_as_float(s_idx[w]);
+            }
+            c_part[0] = a;
+            c_part[1] = b;
+        }
+        cl.sync();  // also publishes this CTA's rows of X_new to the cluster
+        double D = 0.0, Nn = 0.0;
+        for (int q = 0; q < CL; q++) {  // same order in every CTA: same decision
+            D += (double)*cl.map_shared_rank(&c_part[0], q);
+            Nn += (double)*cl.map_shared_rank(&c_part[1], q);
+        }
+        const double rel_step = sqrt(D) / sqrt(Nn);
+        const bool unscaled = !scaling;
+        if (rel_step <= d.tol || (unscaled && prev_rel <= 1e-10) ||
+            (unscaled && prev_rel < 1e-8 && rel_step > 0.5 * prev_rel)) {
+            converged = true;
+            break;
+        }
+        if (rel_step < 1e-2) scaling = false;
+        prev_rel = rel_step;
+        if (!(Nn == Nn)) break;
+        // the partial sums are rewritten only after n more cluster barriers,
+        // which every CTA reaches after these reads
+    }
+    if (g == 0 && tid == 0) {
+        *d.iters = iter;
+        if (bad) atomicExch(d.status, OVL_ENOCONV);
+        else if (!converged) atomicCAS(d.status, 0, OVL_ENOCONV);
+    }
+    cl.sync();  // no CTA leaves while another may read its shared memory
+}
+
+size_t cl_smem_bytes(int n, int CL) {
+    const size_t nrmax = (size_t)((n + CL - 1) / CL);
+    size_t b = nrmax * n * sizeof(float4);             // rows
+    b += 3 * (size_t)n * sizeof(float4);               // 2 candidate rows + pivot row
+    b += (size_t)((nrmax + 1) & ~(size_t)1) * sizeof(float4);
+    b += 2 * (size_t)n * sizeof(int) + (size_t)n + 64;
+    return (b + 15) & ~(size_t)15;
+}
+
+}  // namespace
+
+int ovl_newton_cl_plan(ovl_lattice lat, int nmax, int* cl_size, size_t* smem_out) {
+    *cl_size = 0;
+    *smem_out = 0;
+    int optin = 0, dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return OVL_OK;
+    const size_t avail = (size_t)optin - 1024;  // static shared memory of the kernel
+    if (cudaFuncSetAttribute((const void*)k_newton_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return OVL_OK;
+    }
+    for (int CL : {16, 8}) {
+        const size_t smem = cl_smem_bytes(nmax, CL);
+        if (smem > avail) continue;
+        if (cudaFuncSetAttribute((const void*)k_newton_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = CL;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(CL);
+        cfg.blockDim = dim3(NTC);
+        cfg.dynamicSmemBytes = smem;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, (const void*)k_newton_cl, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (nclusters >= 1) {
+            *cl_size = CL;
+            *smem_out = smem;
+            return OVL_OK;
+        }
+    }
+    (void)lat;
+    return OVL_OK;
+}
+
+int ovl_newton_cl_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int cl_size, size_t smem, cudaStream_t st) {
+    OVL_CUDA_TRY(lat, cudaFuncSetAttribute((const void*)k_newton_cl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cl_size;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(nsolve * cl_size);
+    cfg.blockDim = dim3(NTC);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    OVL_CUDA_TRY(lat, cudaLaunchKernelEx(&cfg, k_newton_cl, nd_dev, nsolve));
+    lat->launches++;
+    return OVL_OK;
+}

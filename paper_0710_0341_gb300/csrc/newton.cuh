@@ -32,4 +32,8 @@ int ovl_newton_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int cpm, c
 int ovl_newton_df_plan(ovl_lattice lat, int nsolve, int nmax, int* cpm, int* smem_rows);
 int ovl_newton_df_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int nmax, int cpm, int smem_rows,
                          cudaStream_t st);
+// double-float Gauss-Jordan Newton, one thread-block cluster per matrix (rows in
+// the cluster's shared memory); cl_size 0 when no cluster shape fits n
+int ovl_newton_cl_plan(ovl_lattice lat, int nmax, int* cl_size, size_t* smem);
+int ovl_newton_cl_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int cl_size, size_t smem, cudaStream_t st);
 int ovl_fmatvec_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int nmax, cudaStream_t st);

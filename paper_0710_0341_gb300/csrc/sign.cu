@@ -200,6 +200,7 @@ struct SolvePlan {
     double2 *u = nullptr, *w = nullptr, *H = nullptr;
     float2* H32 = nullptr;
     double2 *dots = nullptr, *dvec = nullptr;
+    float2* dpart = nullptr;
     float2 *ap = nullptr, *gh = nullptr, *gl = nullptr;
     double* scal = nullptr;
     const float2** qhi = nullptr;
@@ -288,6 +289,7 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             t(p.H32, ld * ld);
             t(p.dots, 2 * ld + 3);
             t(p.dvec, ld + 1);
+            t(p.dpart, ((ld + 63) / 64) * ld);
             t(p.ap, ld);
             t(p.gh, ld);
             t(p.gl, ld);
@@ -408,6 +410,7 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         s.H32 = p.H32;
         s.dots = p.dots;
         s.dvec = p.dvec;
+        s.dpart = p.dpart;
         s.ap = p.ap;
         s.gh = p.gh;
         s.gl = p.gl;
@@ -596,7 +599,7 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             q.iters = p.iters;
             q.cvec = p.cvec;
             q.gout = gout[i];
-            q.df = params[0].newton_fp64 ? 0 : 1;
+            q.df = params[0].newton_fp64 == 1 ? 0 : 1;
             q.crow = p.crow;
             q.Wg = (float4*)p.W;
             if (q.run) {
@@ -621,8 +624,13 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             int cpm_run = ovl_newton_cpm(lat, nsolve, nmax_run);
             (void)cpm;
             ProfScope pn(lat, 5, 0.0, st);
-            if (params[0].newton_fp64) {
+            int cl_size = 0;
+            size_t cl_smem = 0;
+            if (params[0].newton_fp64 == 0) ovl_newton_cl_plan(lat, nmax_run, &cl_size, &cl_smem);
+            if (params[0].newton_fp64 == 1) {
                 if (int rc = ovl_newton_launch(lat, d_nd, nsolve, cpm_run, st)) return rc;
+            } else if (cl_size > 0) {
+                if (int rc = ovl_newton_cl_launch(lat, d_nd, nsolve, cl_size, cl_smem, st)) return rc;
             } else {
                 int cpm_df = 1, smem_rows = 0;
                 ovl_newton_df_plan(lat, nsolve, nmax_run, &cpm_df, &smem_rows);

@@ -8,6 +8,9 @@ so the expensive eigensolver setup is skipped), inside an NVTX range
 
     ncu --set full --clock-control none -k regex:k_gs_update -s 200 -c 1 \\
         python -m paper_0710_0341_gb300.profile_case
+
+``python -m paper_0710_0341_gb300.profile_case stencil r12`` instead applies the
+stencil alone (24^3x48, one right-hand side, 12-real links) five times.
 """
 import numpy as np
 import torch
@@ -41,5 +44,26 @@ def main():
     print("profile case done; newton iterations", [i["newton_iters"] for i in infos])
 
 
+def stencil(fmt_name="r12", dims=(24, 24, 24, 48), reps=5):
+    """Repeated single-RHS stencil applications on packed spinors (24^3x48)."""
+    build.build()
+    V = int(np.prod(dims))
+    h = ovl.ovl_create_lattice(dims)
+    ovl.ovl_set_links(h, torch.from_numpy(synth.random_su3_field(dims, 0.3, 0)).cuda())
+    fmt, links = {"r12": (1, 2), "f32": (1, 1), "f64": (0, 0)}[fmt_name]
+    x = torch.randn(12 * V, dtype=torch.complex64 if fmt == 1 else torch.complex128, device="cuda")
+    o = torch.zeros_like(x)
+    for _ in range(reps):
+        ovl.ovl_apply_Hw_packed(h, [0.3], -1.0, x, o, 1, fmt, links)
+    torch.cuda.synchronize()
+    ovl.ovl_destroy_lattice(h)
+    print("stencil case done", fmt_name, dims)
+
+
 if __name__ == "__main__":
-    main()
+    import sys
+
+    if len(sys.argv) > 1 and sys.argv[1] == "stencil":
+        stencil(*(sys.argv[2:3] or ["r12"]))
+    else:
+        main()
