@@ -72,10 +72,14 @@ typedef struct {
     int    prec;        /* OVL_PREC_* */
     int    newton_max_iter;  /* <= 0: default 100 */
     double newton_tol;       /* <= 0: default 1e-13 (relative Frobenius step) */
-    int    newton_fp64;      /* 0: double-float Gauss-Jordan (default: one thread-block cluster
-                              * per matrix when its rows fit the cluster's shared memory, else
-                              * the cooperative kernel); 1: FP64 Gauss-Jordan; 2: double-float,
-                              * always the cooperative kernel */
+    int    newton_fp64;      /* 0 (default): double-float Gauss-Jordan Newton (one thread-block
+                              * cluster per matrix when its rows fit the cluster's shared memory,
+                              * else the cooperative kernel), finished by Newton-Schulz steps
+                              * once a step is below 1e-2 and |I - X^2|_F < 1/2;
+                              * 1: FP64 Gauss-Jordan Newton; 2: double-float Gauss-Jordan Newton,
+                              * cooperative kernel only; 3: as 0 without Newton-Schulz;
+                              * 4: as 0 with every Newton-Schulz step declined, so that the
+                              * iteration returns to Gauss-Jordan (tests that path) */
     /* Adaptive Krylov depth (not in the paper): with adapt_every = d > 0 the
      * solve starts checking at depth k and then every d steps up to k_max:
      * the estimate est_j = |g_j - (g_{j-d}; 0)| / |g_j| compares the

@@ -349,12 +349,13 @@ __global__ void __launch_bounds__(NTD, 1) k_newton_df(NewtonDev* nds, int nsolve
     __shared__ double s_cv[64];
     __shared__ int s_cr[64];
     unsigned gen = 0;
-    // X_0 = H (column-major FP64 input)
-    for (int r = 0; r < nr; r++) {
-        int i = g + cpm * r;
-        for (int l = tid; l < n; l += NTD) X[(size_t)i * n + l] = dfc_pack(dfc_from(d.H[i + (size_t)l * d.ldH]));
-    }
-    bool scaling = true, converged = false;
+    // X_0 = H (column-major FP64 input); on resume X holds the iterate
+    if (!d.resume)
+        for (int r = 0; r < nr; r++) {
+            int i = g + cpm * r;
+            for (int l = tid; l < n; l += NTD) X[(size_t)i * n + l] = dfc_pack(dfc_from(d.H[i + (size_t)l * d.ldH]));
+        }
+    bool scaling = !d.resume, converged = false, handoff = false;
     double prev_rel = 1e300;
     int iter = 0;
     if (!group_sync(d, gen, cpm)) return;
@@ -532,13 +533,18 @@ __global__ void __launch_bounds__(NTD, 1) k_newton_df(NewtonDev* nds, int nsolve
             converged = true;
             break;
         }
+        if (d.ns_switch > 0.0 && rel_step < d.ns_switch) {  // Newton-Schulz takes over
+            handoff = true;
+            break;
+        }
         if (rel_step < 1e-2) scaling = false;
         prev_rel = rel_step;
         if (!(Nn == Nn)) break;
     }
     if (g == 0 && tid == 0) {
         *d.iters = iter;
-        if (!converged) atomicCAS(d.status, 0, OVL_ENOCONV);
+        if (handoff) *d.handoff = 1;
+        else if (!converged) atomicCAS(d.status, 0, OVL_ENOCONV);
     }
 }
 
@@ -662,12 +668,13 @@ __global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve
     __shared__ float4 s_inv;
     __shared__ float s_mant;
     __shared__ int s_exp;
-    // X_0 = H (column-major FP64 input), own rows
-    for (int r = 0; r < nr; r++) {
-        const int i = g + CL * r;
-        for (int l = tid; l < n; l += NTC) X[(size_t)i * n + l] = dfc_pack(dfc_from(d.H[i + (size_t)l * d.ldH]));
-    }
-    bool scaling = true, converged = false, bad = false;
+    // X_0 = H (column-major FP64 input), own rows; on resume X holds the iterate
+    if (!d.resume)
+        for (int r = 0; r < nr; r++) {
+            const int i = g + CL * r;
+            for (int l = tid; l < n; l += NTC) X[(size_t)i * n + l] = dfc_pack(dfc_from(d.H[i + (size_t)l * d.ldH]));
+        }
+    bool scaling = !d.resume, converged = false, bad = false, handoff = false;
     double prev_rel = 1e300;
     int iter = 0;
     __syncthreads();
@@ -848,6 +855,10 @@ __global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve
             converged = true;
             break;
         }
+        if (d.ns_switch > 0.0 && rel_step < d.ns_switch) {  // Newton-Schulz takes over
+            handoff = true;
+            break;
+        }
         if (rel_step < 1e-2) scaling = false;
         prev_rel = rel_step;
         if (!(Nn == Nn)) break;
@@ -857,6 +868,7 @@ __global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve
     if (g == 0 && tid == 0) {
         *d.iters = iter;
         if (bad) atomicExch(d.status, OVL_ENOCONV);
+        else if (handoff) *d.handoff = 1;
         else if (!converged) atomicCAS(d.status, 0, OVL_ENOCONV);
     }
     cl.sync();  // no CTA leaves while another may read its shared memory
@@ -873,7 +885,11 @@ size_t cl_smem_bytes(int n, int CL) {
 
 }  // namespace
 
-int ovl_newton_cl_plan(ovl_lattice lat, int nmax, int* cl_size, size_t* smem_out) {
+int ovl_newton_cl_plan(ovl_lattice lat, int nsolve, int nmax, int* cl_size, size_t* smem_out) {
+    // Cluster size: the rows must fit the cluster's shared memory, and a GPC
+    // hosts one cluster of 16 at most (a floor-swept GPC none), so a smaller
+    // cluster can keep every matrix of the batch resident in one wave. The
+    // cost of a size is waves x rows per CTA (the per-pivot work of a CTA).
     *cl_size = 0;
     *smem_out = 0;
     int optin = 0, dev = 0;
@@ -885,14 +901,15 @@ int ovl_newton_cl_plan(ovl_lattice lat, int nmax, int* cl_size, size_t* smem_out
         cudaGetLastError();
         return OVL_OK;
     }
-    for (int CL : {16, 8}) {
+    if (cudaFuncSetAttribute((const void*)k_newton_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)avail) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return OVL_OK;
+    }
+    long best_cost = -1;
+    for (int CL = 16; CL >= 2; CL--) {
         const size_t smem = cl_smem_bytes(nmax, CL);
-        if (smem > avail) continue;
-        if (cudaFuncSetAttribute((const void*)k_newton_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
+        if (smem > avail) break;  // smaller clusters need more shared memory per CTA
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -904,15 +921,18 @@ int ovl_newton_cl_plan(ovl_lattice lat, int nmax, int* cl_size, size_t* smem_out
         cfg.dynamicSmemBytes = smem;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, (const void*)k_newton_cl, &cfg) != cudaSuccess) {
+        int active = 0;
+        if (cudaOccupancyMaxActiveClusters(&active, (const void*)k_newton_cl, &cfg) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
-        if (nclusters >= 1) {
+        if (active < 1) continue;
+        const long waves = (nsolve + active - 1) / active;
+        const long cost = waves * (long)((nmax + CL - 1) / CL);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
             *cl_size = CL;
             *smem_out = smem;
-            return OVL_OK;
         }
     }
     (void)lat;

@@ -14,10 +14,16 @@
 #include <math.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "df.cuh"
 #include "krylov.cuh"
 #include "newton.cuh"
+
+// Newton-Schulz takes over from the scaled Newton iteration once a step is
+// below NS_SWITCH (relative, Frobenius); at most NS_MAX_ITER products steps
+static constexpr double NS_SWITCH = 1e-2;
+static constexpr int NS_MAX_ITER = 40;
 
 namespace {
 
@@ -205,7 +211,9 @@ struct SolvePlan {
     double* scal = nullptr;
     const float2** qhi = nullptr;
     const float2** qlo = nullptr;
-    double2 *X = nullptr, *W = nullptr;
+    double2 *X = nullptr, *W = nullptr, *Yns = nullptr;
+    double* nsacc = nullptr;
+    int* handoff = nullptr;
     float4* crow = nullptr;
     double *cand_val = nullptr, *red = nullptr;
     int* cand_row = nullptr;
@@ -237,6 +245,9 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         const ovl_sign_params& q = params[i];
         if (q.prec != prec) return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: mixed precisions in one batch");
         if (q.m_w != m_w) return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: one m_w per batch");
+        if (q.newton_fp64 != params[0].newton_fp64 || q.newton_fp64 < 0 || q.newton_fp64 > 4)
+            return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: solve %d: newton_fp64=%d (0..4, one per batch)", i,
+                            q.newton_fp64);
         if (!(q.m_w > -4.0 + 1e-12) || !(q.mu == q.mu) || fabs(q.mu) > 50.0)
             return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: solve %d: bad mu/m_w", i);
         if (q.k < 1) return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: solve %d: k=%d < 1", i, q.k);
@@ -298,6 +309,9 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             t(p.qlo, ld);
             t(p.X, nm * nm);
             t(p.W, nm * nm + 64 * nm);
+            t(p.Yns, nm * nm);
+            t(p.nsacc, OVL_NS_ACC);
+            t(p.handoff, 1);
             t(p.crow, 2 * 64 * nm);
             t(p.cand_val, 128);
             t(p.cand_row, 128);
@@ -326,23 +340,38 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         return c.off;
     };
     size_t per = plan_bytes(false, nullptr);
-    size_t batch_off;
-    {
-        Carve c{nullptr};
-        c.off = per;
-        c.take<SolveDev>(nsolve);
-        c.take<SolveDev>(nsolve);
-        c.take<NewtonDev>(nsolve);
-        c.take<ProjDev>(nsolve);
-        c.take<GemvDev>(nsolve);
-        c.take<double2>((size_t)nsolve * G * pstride);
-        c.take<int>(nsolve);
-        c.take<double>(nsolve);
-        c.take<void*>(2 * (size_t)nsolve);
-        c.take<double2>(N * nsolve);  // canonical staging for host b / y
-        c.take<char>(0);
-        batch_off = c.off;
-    }
+    // batch-wide pieces after the per-solve ones: one routine sizes and carves
+    struct BatchPtrs {
+        SolveDev *sd = nullptr, *sd_est = nullptr;
+        NewtonDev* nd = nullptr;
+        NsDev* ns = nullptr;
+        ProjDev* pd = nullptr;
+        GemvDev* gd = nullptr;
+        double2* part = nullptr;
+        int* counters = nullptr;
+        double* mu = nullptr;
+        void** ptrs = nullptr;
+        double2* canon = nullptr;  // canonical staging for host b / y
+    };
+    auto carve_batch = [&](char* at) -> std::pair<BatchPtrs, size_t> {
+        Carve cb{at};
+        cb.off = per;
+        BatchPtrs q;
+        q.sd = cb.take<SolveDev>(nsolve);
+        q.sd_est = cb.take<SolveDev>(nsolve);
+        q.nd = cb.take<NewtonDev>(nsolve);
+        q.ns = cb.take<NsDev>(nsolve);
+        q.pd = cb.take<ProjDev>(nsolve);
+        q.gd = cb.take<GemvDev>(nsolve);
+        q.part = cb.take<double2>((size_t)nsolve * G * pstride);
+        q.counters = cb.take<int>(nsolve);
+        q.mu = cb.take<double>(nsolve);
+        q.ptrs = cb.take<void*>(2 * (size_t)nsolve);
+        q.canon = cb.take<double2>(N * nsolve);
+        cb.take<char>(0);
+        return {q, cb.off};
+    };
+    const size_t batch_off = carve_batch(nullptr).second;
     if (batch_off > lat->ws_bytes) {
         cudaStreamSynchronize(lat->stream);
         cudaFree(lat->ws);
@@ -356,18 +385,18 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     }
     char* base = (char*)lat->ws;
     plan_bytes(true, base);
-    Carve c{base};
-    c.off = per;
-    SolveDev* d_sd = c.take<SolveDev>(nsolve);
-    SolveDev* d_sd_est = c.take<SolveDev>(nsolve);
-    NewtonDev* d_nd = c.take<NewtonDev>(nsolve);
-    ProjDev* d_pd = c.take<ProjDev>(nsolve);
-    GemvDev* d_gd = c.take<GemvDev>(nsolve);
-    double2* d_part = c.take<double2>((size_t)nsolve * G * pstride);
-    int* d_counters = c.take<int>(nsolve);
-    double* d_mu = c.take<double>(nsolve);
-    void** d_ptrs = c.take<void*>(2 * (size_t)nsolve);
-    double2* d_canon = c.take<double2>(N * nsolve);
+    const BatchPtrs bp = carve_batch(base).first;
+    SolveDev* d_sd = bp.sd;
+    SolveDev* d_sd_est = bp.sd_est;
+    NewtonDev* d_nd = bp.nd;
+    NsDev* d_ns = bp.ns;
+    ProjDev* d_pd = bp.pd;
+    GemvDev* d_gd = bp.gd;
+    double2* d_part = bp.part;
+    int* d_counters = bp.counters;
+    double* d_mu = bp.mu;
+    void** d_ptrs = bp.ptrs;
+    double2* d_canon = bp.canon;
     cudaStream_t st = lat->stream;
 
     // ---- inputs ----
@@ -602,6 +631,9 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             q.df = params[0].newton_fp64 == 1 ? 0 : 1;
             q.crow = p.crow;
             q.Wg = (float4*)p.W;
+            q.ns_switch = (params[0].newton_fp64 == 0 || params[0].newton_fp64 == 4) ? NS_SWITCH : 0.0;
+            q.resume = 0;
+            q.handoff = p.handoff;
             if (q.run) {
                 any_run = 1;
                 nmax_run = std::max(nmax_run, n);
@@ -617,6 +649,7 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             OVL_CUDA_TRY(lat, cudaMemsetAsync(p.bar, 0, sizeof(unsigned), st));
             OVL_CUDA_TRY(lat, cudaMemsetAsync(p.nstat, 0, sizeof(int), st));
             OVL_CUDA_TRY(lat, cudaMemsetAsync(p.iters, 0, sizeof(int), st));
+            OVL_CUDA_TRY(lat, cudaMemsetAsync(p.handoff, 0, sizeof(int), st));
             OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
         }
         OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_nd, nd.data(), nsolve * sizeof(NewtonDev), cudaMemcpyHostToDevice, st));
@@ -624,17 +657,81 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             int cpm_run = ovl_newton_cpm(lat, nsolve, nmax_run);
             (void)cpm;
             ProfScope pn(lat, 5, 0.0, st);
-            int cl_size = 0;
+            // 0: cluster (else cooperative) double-float Gauss-Jordan, Newton-Schulz finish;
+            // 1: FP64 Gauss-Jordan; 2: cooperative double-float only; 3: cluster (else
+            // cooperative) double-float only; 4: as 0 with every Newton-Schulz step
+            // declined (the return to Gauss-Jordan)
+            const int mode = params[0].newton_fp64;
+            int cl_size = 0, cpm_df = 1, smem_rows = 0;
             size_t cl_smem = 0;
-            if (params[0].newton_fp64 == 0) ovl_newton_cl_plan(lat, nmax_run, &cl_size, &cl_smem);
-            if (params[0].newton_fp64 == 1) {
-                if (int rc = ovl_newton_launch(lat, d_nd, nsolve, cpm_run, st)) return rc;
-            } else if (cl_size > 0) {
-                if (int rc = ovl_newton_cl_launch(lat, d_nd, nsolve, cl_size, cl_smem, st)) return rc;
-            } else {
-                int cpm_df = 1, smem_rows = 0;
-                ovl_newton_df_plan(lat, nsolve, nmax_run, &cpm_df, &smem_rows);
-                if (int rc = ovl_newton_df_launch(lat, d_nd, nsolve, nmax_run, cpm_df, smem_rows, st)) return rc;
+            if (mode == 0 || mode == 3 || mode == 4) ovl_newton_cl_plan(lat, nsolve, nmax_run, &cl_size, &cl_smem);
+            if (mode != 1 && cl_size == 0) ovl_newton_df_plan(lat, nsolve, nmax_run, &cpm_df, &smem_rows);
+            auto launch_gj = [&]() -> int {
+                if (mode == 1) return ovl_newton_launch(lat, d_nd, nsolve, cpm_run, st);
+                if (cl_size > 0) return ovl_newton_cl_launch(lat, d_nd, nsolve, cl_size, cl_smem, st);
+                return ovl_newton_df_launch(lat, d_nd, nsolve, nmax_run, cpm_df, smem_rows, st);
+            };
+            if (int rc = launch_gj()) return rc;
+            if (mode == 0 || mode == 4) {
+                std::vector<int> hf(nsolve, 0), it_gj(nsolve, 0);
+                for (int i = 0; i < nsolve; i++) {
+                    if (!nd[i].run) continue;
+                    OVL_CUDA_TRY(lat, cudaMemcpyAsync(&hf[i], P[i].handoff, sizeof(int), cudaMemcpyDeviceToHost, st));
+                    OVL_CUDA_TRY(lat, cudaMemcpyAsync(&it_gj[i], P[i].iters, sizeof(int), cudaMemcpyDeviceToHost, st));
+                }
+                OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
+                std::vector<NsDev> hn(nsolve);
+                bool any_ns = false;
+                for (int i = 0; i < nsolve; i++) {
+                    NsDev& z = hn[i];
+                    memset(&z, 0, sizeof z);
+                    z.X = (float4*)P[i].X;
+                    z.W = (float4*)P[i].W;
+                    z.Y = (float4*)P[i].Yns;
+                    z.acc = P[i].nsacc;
+                    z.n = nd[i].n;
+                    z.on = nd[i].run && hf[i];
+                    z.tol = nd[i].tol;
+                    z.prev = 1e300;
+                    z.region = mode == 4 ? 0.0 : 0.25;
+                    any_ns = any_ns || z.on;
+                }
+                if (any_ns) {
+                    if (int rc = ovl_newton_schulz(lat, d_ns, hn.data(), nsolve, nmax_run, NS_MAX_ITER, st)) return rc;
+                    // matrices that left the Newton-Schulz region go back to Gauss-Jordan
+                    std::vector<int> run0(nsolve), tot(nsolve);
+                    bool any_fb = false;
+                    for (int i = 0; i < nsolve; i++) {
+                        run0[i] = nd[i].run;
+                        tot[i] = it_gj[i] + hn[i].iters;
+                        nd[i].run = run0[i] && hf[i] && hn[i].fallback;
+                        nd[i].resume = 1;
+                        nd[i].ns_switch = 0.0;
+                        any_fb = any_fb || nd[i].run;
+                    }
+                    if (any_fb) {
+                        for (int i = 0; i < nsolve; i++)  // the cooperative kernel's barrier starts at zero
+                            if (nd[i].run) OVL_CUDA_TRY(lat, cudaMemsetAsync(P[i].bar, 0, sizeof(unsigned), st));
+                        OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_nd, nd.data(), nsolve * sizeof(NewtonDev),
+                                                          cudaMemcpyHostToDevice, st));
+                        if (int rc = launch_gj()) return rc;
+                        std::vector<int> it2(nsolve, 0);
+                        for (int i = 0; i < nsolve; i++)
+                            if (nd[i].run)
+                                OVL_CUDA_TRY(lat, cudaMemcpyAsync(&it2[i], P[i].iters, sizeof(int),
+                                                                  cudaMemcpyDeviceToHost, st));
+                        OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
+                        for (int i = 0; i < nsolve; i++) tot[i] += it2[i];
+                    }
+                    for (int i = 0; i < nsolve; i++) {
+                        nd[i].run = run0[i];
+                        if (run0[i] && hf[i])
+                            OVL_CUDA_TRY(lat, cudaMemcpyAsync(P[i].iters, &tot[i], sizeof(int), cudaMemcpyHostToDevice, st));
+                    }
+                    OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_nd, nd.data(), nsolve * sizeof(NewtonDev),
+                                                      cudaMemcpyHostToDevice, st));
+                    OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));  // tot, nd must outlive the copies
+                }
             }
             if (int rc = ovl_fmatvec_launch(lat, d_nd, nsolve, nmax_run, st)) return rc;
             pn.end(st);

@@ -254,9 +254,11 @@ def test_newton_double_float_matches_fp64_newton():
 @pytest.mark.parametrize("ks", [(300, 460), (520,)])
 def test_newton_kernels_large_projected_matrix(ks):
     """Projected matrices of order 300-520 (4^4, no deflation): at n <= 460 the
-    rows fit a 16-CTA cluster's shared memory (cluster kernel, the default), at
-    n = 520 they do not (cooperative kernel). Every Newton variant (default,
-    FP64, cooperative double-float) matches the oracle's Eq. 11 result."""
+    rows fit a 16-CTA cluster's shared memory (cluster kernel), at n = 520 they
+    do not (cooperative kernel). Every variant of the small sign (default with
+    the Newton-Schulz finish, FP64, cooperative double-float, cluster without
+    Newton-Schulz, Newton-Schulz declined and resumed by Gauss-Jordan) matches
+    the oracle's Eq. 11 result and the FP64 Newton."""
     need_gpu()
     dims, mu, m_w = (4, 4, 4, 4), 0.3, -1.0
     U, A = _setup(dims, 0.5, mu, m_w)
@@ -265,15 +267,15 @@ def test_newton_kernels_large_projected_matrix(ks):
     try:
         bb = np.stack([b] * len(ks))
         ys = {}
-        for mode in (0, 1, 2):
+        for mode in (0, 1, 2, 3, 4):
             ys[mode] = np.zeros_like(bb)
             infos = ovl.ovl_sign_apply(h, [dict(mu=mu, m_w=m_w, k=k, newton_fp64=mode) for k in ks],
                                        [None] * len(ks), bb, ys[mode])
             assert all(i["status"] == 0 and i["newton_iters"] > 0 for i in infos)
         for i, k in enumerate(ks):
             yo = krylov.sign_arnoldi(A, b.ravel(), k)
-            for mode in (0, 1, 2):
+            for mode in (0, 1, 2, 3, 4):
                 assert rel(ys[mode][i], yo) < 1e-10, (k, mode, rel(ys[mode][i], yo))
-            assert rel(ys[0][i], ys[1][i]) < 1e-11, (k, rel(ys[0][i], ys[1][i]))
+                assert rel(ys[mode][i], ys[1][i]) < 1e-11, (k, mode, rel(ys[mode][i], ys[1][i]))
     finally:
         ovl.ovl_destroy_lattice(h)
