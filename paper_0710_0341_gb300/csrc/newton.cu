@@ -596,7 +596,14 @@ int ovl_newton_df_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int nma
 // copies it to a double-buffered candidate slot in its own shared memory,
 // the cluster meets at one hardware barrier, and every CTA reads the
 // candidates and then the winning row straight out of the owner's shared
-// memory (distributed shared memory). Clusters never wait on each other, so
+// memory (distributed shared memory). The barrier is split (arrive, wait) with
+// one step of lookahead: after the pivot row is known, a CTA first updates
+// column k+1 of its rows, picks and fully updates its candidate for k+1,
+// publishes it and arrives, and only then updates the rest of its rows, so
+// the barrier and the candidate exchange overlap the bulk of the update.
+// Candidate slots alternate by pivot parity: a slot is rewritten only after a
+// barrier that every reader of its previous contents has passed.
+// Clusters never wait on each other, so
 // the launch is not cooperative: more matrices than resident clusters simply
 // run in waves. All branches that skip a barrier (no work, singular pivot)
 // are taken by every CTA of a cluster alike, since they depend only on data
@@ -636,6 +643,11 @@ __device__ __forceinline__ dfc dfc_inv(const dfc& z) {
     const dfc zc = dfc_make(make_float2(z.hi.x, -z.hi.y), make_float2(z.lo.x, -z.lo.y));
     return dfc_mul(zc, dfc_make(make_float2(rh, 0.f), make_float2(rl, 0.f)));
 }
+
+// split cluster barrier (release on arrive, acquire on wait); every thread
+// alternates arrive and wait, and cluster.sync() is one arrive plus one wait
+__device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
 __global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve) {
     extern __shared__ float4 csm[];
@@ -677,6 +689,53 @@ __global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve
     bool scaling = !d.resume, converged = false, bad = false, handoff = false;
     double prev_rel = 1e300;
     int iter = 0;
+    // this CTA's best unused row for column col (largest |hi|^2, then smallest
+    // row), brought up to date by row_update, copied to candidate slot `slot`
+    // and published with its value; returns its own index (or -1)
+    auto select_publish = [&](int col, int slot, auto&& row_update) -> int {
+        float best = -1.f;
+        int br = -1;
+        for (int r = tid; r < nr; r += NTC) {
+            if (used[g + CL * r]) continue;
+            const float4 v = R[(size_t)r * n + col];
+            const float a = v.x * v.x + v.y * v.y;
+            if (a > best) {
+                best = a;
+                br = r;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, br, o);
+            if (ov > best || (ov == best && oi >= 0 && (br < 0 || oi < br))) {
+                best = ov;
+                br = oi;
+            }
+        }
+        if (lane == 0) {
+            s_red[warp] = best;
+            s_idx[warp] = br;
+        }
+        __syncthreads();
+        best = s_red[0];
+        br = s_idx[0];
+        for (int w = 1; w < NTC / 32; w++)
+            if (s_red[w] > best || (s_red[w] == best && s_idx[w] >= 0 && (br < 0 || s_idx[w] < br))) {
+                best = s_red[w];
+                br = s_idx[w];
+            }
+        if (br >= 0)
+            for (int l = tid; l < n; l += NTC) {
+                row_update(br, l);
+                crow[(size_t)slot * n + l] = R[(size_t)br * n + l];
+            }
+        if (tid == 0) {
+            c_val[slot] = br >= 0 ? best : -1.f;
+            c_row[slot] = br >= 0 ? g + CL * br : 0x7fffffff;
+        }
+        return br;
+    };
     __syncthreads();
     while (iter < d.max_iter) {
         iter++;
@@ -690,47 +749,14 @@ __global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve
             s_exp = 0;
         }
         __syncthreads();
+        // candidates for column 0 (rows fully current), then one split cluster
+        // barrier per pivot: arrive once the next candidate is published,
+        // wait before reading the candidates
+        select_publish(0, 0, [](int, int) {});
+        cl_arrive();
         for (int k = 0; k < n; k++) {
             const int slot = k & 1;
-            float best = -1.f;
-            int br = -1;
-            for (int r = tid; r < nr; r += NTC) {
-                if (used[g + CL * r]) continue;
-                const float4 v = R[(size_t)r * n + k];
-                const float a = v.x * v.x + v.y * v.y;
-                if (a > best) {
-                    best = a;
-                    br = r;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ov = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, br, o);
-                if (ov > best || (ov == best && oi >= 0 && (br < 0 || oi < br))) {
-                    best = ov;
-                    br = oi;
-                }
-            }
-            if (lane == 0) {
-                s_red[warp] = best;
-                s_idx[warp] = br;
-            }
-            __syncthreads();
-            best = s_red[0];
-            br = s_idx[0];
-            for (int w = 1; w < NTC / 32; w++)
-                if (s_red[w] > best || (s_red[w] == best && s_idx[w] >= 0 && (br < 0 || s_idx[w] < br))) {
-                    best = s_red[w];
-                    br = s_idx[w];
-                }
-            if (br >= 0)
-                for (int l = tid; l < n; l += NTC) crow[(size_t)slot * n + l] = R[(size_t)br * n + l];
-            if (tid == 0) {
-                c_val[slot] = br >= 0 ? best : -1.f;
-                c_row[slot] = br >= 0 ? g + CL * br : 0x7fffffff;
-            }
-            cl.sync();
+            cl_wait();
             // winner over the cluster: largest |pivot|^2, then smallest row
             if (warp == 0) {
                 float v = -1.f;
@@ -780,18 +806,31 @@ __global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve
             for (int l = tid; l < n; l += NTC) prow[l] = l == k ? s_inv : dfc_pack(dfc_mul(dfc_unpack(pw[l]), inv));
             __syncthreads();
             const int rp = (pr % CL == g) ? (pr - g) / CL : -1;  // own index of the pivot row
-            // every (own row, column) pair once, flattened over the CTA
+            // x <- x - f p for own row r != rp at column l (column k: 0 - f p)
+            auto upd = [&](int r, int l) {
+                float4* x = R + (size_t)r * n + l;
+                if (r == rp) {
+                    *x = prow[l];
+                } else {
+                    const dfc pl = dfc_unpack(prow[l]);
+                    const dfc f = dfc_unpack(fcol[r]);
+                    *x = dfc_pack(dfc_fms(l == k ? dfc_zero() : dfc_unpack(*x), f, pl));
+                }
+            };
+            int skip_r = -1, skip_l = -1;  // already updated: the published row, column k + 1
+            if (k + 1 < n) {
+                // lookahead: column k + 1, the next candidate row, publish, arrive
+                for (int r = tid; r < nr; r += NTC) upd(r, k + 1);
+                __syncthreads();
+                skip_r = select_publish(k + 1, (k + 1) & 1, [&](int r, int l) { if (l != k + 1) upd(r, l); });
+                skip_l = k + 1;
+                cl_arrive();
+            }
+            // every remaining (own row, column) pair once, flattened over the CTA
             int r = tid / n, l = tid - (tid / n) * n;
             const int total = nr * n;
             for (int e = tid; e < total; e += NTC) {
-                const dfc pl = dfc_unpack(prow[l]);
-                if (r == rp) {
-                    R[(size_t)r * n + l] = prow[l];
-                } else {
-                    const dfc f = dfc_unpack(fcol[r]);
-                    float4* x = R + (size_t)r * n + l;
-                    *x = dfc_pack(dfc_fms(l == k ? dfc_zero() : dfc_unpack(*x), f, pl));
-                }
+                if (r != skip_r && l != skip_l) upd(r, l);
                 l += NTC;
                 while (l >= n) {
                     l -= n;
