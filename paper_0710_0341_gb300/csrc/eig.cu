@@ -99,7 +99,7 @@ class Solver {
     Dev mem;
     float2 *Va_hi = nullptr, *Va_lo, *Vb_hi, *Vb_lo;
     double2 *u, *w, *tmp, *H, *dots, *dvec, *part, *Vf, *Wf, *gcoef;
-    float2 *H32, *ap, *gh, *gl, *dpart;
+    float2 *H32, *ap, *gh, *gl;
     double* scal;
     const float2 **qhi, **qlo;
     int* counters;
@@ -133,7 +133,6 @@ class Solver {
         TRYP(H32 = mem.get<float2>(ld * ld));
         TRYP(dots = mem.get<double2>(2 * ld + 3));
         TRYP(dvec = mem.get<double2>(ld + 1));
-        TRYP(dpart = mem.get<float2>(((ld + 63) / 64) * ld));
         TRYP(ap = mem.get<float2>(ld));
         TRYP(gh = mem.get<float2>(ld));
         TRYP(gl = mem.get<float2>(ld));
@@ -285,7 +284,6 @@ class Solver {
             s.H32 = H32;
             s.dots = dots;
             s.dvec = dvec;
-            s.dpart = dpart;
             s.ap = ap;
             s.gh = gh;
             s.gl = gl;

@@ -55,6 +55,7 @@ __device__ __forceinline__ bool solve_in_step(const SolveDev& d, int j) {
 // ---------------------------------------------------------------------------
 constexpr int DOTB_RB = 1024;               // rows per block
 constexpr int DOTB_FL = DOTB_RB / 64;       // float4 loads per lane per column (16)
+constexpr int DOT_BATCH = 8;                // loads in flight per lane
 
 __global__ void __launch_bounds__(DOT_THREADS) k_gs_dot(BatchDev B, int j) {
     const int s = blockIdx.y;
@@ -107,16 +108,16 @@ __global__ void __launch_bounds__(DOT_THREADS) k_gs_dot(BatchDev B, int j) {
                 (const float4*)(c < nptr ? s_col[c] : d.vhi + (size_t)(c - nptr) * N) + (base >> 1);
             float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
 #pragma unroll
-            for (int h = 0; h < 2; h++) {  // two batches of 8 loads in flight
-                float4 qq[DOTB_FL / 2];
+            for (int h = 0; h < DOTB_FL / DOT_BATCH; h++) {  // batches of loads in flight
+                float4 qq[DOT_BATCH];
 #pragma unroll
-                for (int i = 0; i < DOTB_FL / 2; i++) {
-                    const int rl = 64 * (h * (DOTB_FL / 2) + i) + 2 * lane;  // local row (even)
+                for (int i = 0; i < DOT_BATCH; i++) {
+                    const int rl = 64 * (h * DOT_BATCH + i) + 2 * lane;  // local row (even)
                     qq[i] = (full || base + rl < N) ? __ldg(q + (rl >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
 #pragma unroll
-                for (int i = 0; i < DOTB_FL / 2; i++) {
-                    const int rl = 64 * (h * (DOTB_FL / 2) + i) + 2 * lane;
+                for (int i = 0; i < DOT_BATCH; i++) {
+                    const int rl = 64 * (h * DOT_BATCH + i) + 2 * lane;
                     const float4 x0 = s_uw[rl], x1 = s_uw[rl + 1];
                     const float4 qv = qq[i];
                     // conj(q) * u and conj(q) * w for rows rl, rl+1
@@ -184,17 +185,11 @@ __global__ void __launch_bounds__(256) k_gs_reduce(BatchDev B, int j, int G_used
 // ---------------------------------------------------------------------------
 // small step: d = H a (FP32 is enough: |a| is at the rounding level of one
 // Gram-Schmidt pass), then nu, c, e and the pass-B coefficients; H update.
-// j < 0: final pass after the last step (only the H update of column p-1).
-//
-// Phase 1 tiles H into 32-row x 64-column blocks (a warp takes 8 columns,
-// a lane one row: 8 independent loads per thread); each tile writes one
-// partial per row, and the last tile of a solve to finish sums the partials
-// in column-tile order (deterministic) and runs phase 2.
+// k_gs_small: one CTA per solve, for the first step (no d) and for the final
+// pass (j < 0: only the H update of column p-1). k_gs_small_rows: every other
+// step, a CTA per 32 rows of d.
 // ---------------------------------------------------------------------------
-constexpr int SM_TR = 32;  // rows per tile
-constexpr int SM_TC = 64;  // columns per tile (8 per warp)
-
-__global__ void __launch_bounds__(256) k_gs_small(BatchDev B, int j, int ctmax) {
+__global__ void __launch_bounds__(256) k_gs_small(BatchDev B, int j) {
     const int s = blockIdx.y;
     SolveDev& d = B.sd[s];
     if (!solve_in_step(d, j)) return;
@@ -202,72 +197,8 @@ __global__ void __launch_bounds__(256) k_gs_small(BatchDev B, int j, int ctmax) 
     const int ld = d.ldH;
     const bool first = (j == 1);
     const bool final_pass = (j < 0);
-    __shared__ float2 red[8][SM_TR];
-    __shared__ int is_last;
     const int tid = threadIdx.x;
     const double2* dots = d.dots;
-    // phase 1: rows of d (not needed for the first step or the final pass)
-    if (!first && !final_pass) {
-        if (d.dpart == nullptr) {  // descriptor without partial buffer: refuse, do not write
-            if (blockIdx.x == 0 && tid == 0) {
-                d.status = OVL_EINVAL;
-                d.active = 0;
-            }
-            return;
-        }
-        const int lane = tid & 31, warp = tid >> 5;
-        const int tr = blockIdx.x / ctmax, tc = blockIdx.x % ctmax;
-        const int row = tr * SM_TR + lane;
-        const int cb = tc * SM_TC + warp * 8;
-        // H is upper Hessenberg below the Schur block: row i has no entries left of column i-1
-        const int cmin = row >= d.m_q + 1 ? row - 1 : 0;
-        float2 acc = make_float2(0.f, 0.f);
-        if (row < p && tc * SM_TC < p) {
-            float2 h[8], av[8];
-#pragma unroll
-            for (int t = 0; t < 8; t++) {
-                const int c = cb + t;
-                const bool on = c < p && c >= cmin;
-                h[t] = on ? d.H32[row + (size_t)c * ld] : make_float2(0.f, 0.f);
-                const double2 a = c < p ? dots[c] : make_double2(0.0, 0.0);
-                av[t] = make_float2((float)a.x, (float)a.y);
-            }
-#pragma unroll
-            for (int t = 0; t < 8; t++) {
-                acc.x = fmaf(h[t].x, av[t].x, fmaf(-h[t].y, av[t].y, acc.x));
-                acc.y = fmaf(h[t].x, av[t].y, fmaf(h[t].y, av[t].x, acc.y));
-            }
-        }
-        red[warp][lane] = acc;
-        __syncthreads();
-        if (warp == 0 && row < p && tc * SM_TC < p) {
-            float2 t = red[0][lane];
-            for (int k = 1; k < 8; k++) {
-                t.x += red[k][lane].x;
-                t.y += red[k][lane].y;
-            }
-            d.dpart[(size_t)tc * ld + row] = t;
-        }
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) is_last = (atomicAdd(&B.counters[s], 1) == (int)gridDim.x - 1);
-        __syncthreads();
-        if (!is_last) return;
-        __threadfence();
-        const int nct = (p + SM_TC - 1) / SM_TC;
-        for (int r = tid; r < p; r += 256) {
-            float2 t = make_float2(0.f, 0.f);
-            for (int c = 0; c < nct; c++) {
-                const float2 v = __ldcg(d.dpart + (size_t)c * ld + r);
-                t.x += v.x;
-                t.y += v.y;
-            }
-            d.dvec[r] = make_double2(t.x, t.y);
-        }
-        __syncthreads();
-    } else if (blockIdx.x != 0) {
-        return;
-    }
     // phase 2: one block per solve
     __shared__ double sh_r[8];
     __shared__ double2 sh_c[8];
@@ -391,6 +322,168 @@ __global__ void __launch_bounds__(256) k_gs_small(BatchDev B, int j, int ctmax) 
         d.gl[c] = make_float2(sx.y, sy.y);
     }
     if (tid == 0) B.counters[s] = 0;
+}
+
+// Small step for j >= 2, one CTA per 32 rows r of the tile [r0, r0 + 32):
+//  d_r = sum_c H32[r][c] a_c, the 16 warps splitting the columns (a lane per
+//  row: coalesced column reads), then the step scalars (nu, c_p, e_p), which
+//  every CTA of the solve computes from the same data in the same order (the
+//  same bits), then column p of H, the correction of column p-1 and the
+//  pass-B coefficients of its own rows. CTA 0 writes the entries of row p and
+//  the scalars of the solve. A CTA writes H only in its own rows and reads
+//  only its own rows of H32, so the CTAs need no ordering among themselves.
+constexpr int SR_ROWS = 32;
+constexpr int SR_THREADS = 512;
+
+__global__ void __launch_bounds__(SR_THREADS) k_gs_small_rows(BatchDev B, int j) {
+    const int s = blockIdx.y;
+    SolveDev& d = B.sd[s];
+    if (!solve_in_step(d, j)) return;
+    const int p = solve_p(d, j);  // >= 1
+    const int r0 = blockIdx.x * SR_ROWS;
+    if (r0 >= p) return;
+    const int ld = d.ldH;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const double2* dots = d.dots;
+    __shared__ float2 red[SR_THREADS / 32][SR_ROWS];
+    __shared__ double sh_r[SR_THREADS / 32];
+    __shared__ double2 sh_c[SR_THREADS / 32];
+    __shared__ double sh_nu, sh_inv, sh_ep_r, sh_ep_i;
+    __shared__ int sh_stop;
+    {
+        const int row = r0 + lane;
+        // H is upper Hessenberg below the Schur block: row i has no entries left of column i-1
+        const int cmin = row >= d.m_q + 1 ? row - 1 : 0;
+        float2 acc = make_float2(0.f, 0.f);
+        if (row < p) {
+#pragma unroll 8
+            for (int c = warp; c < p; c += SR_THREADS / 32) {
+                if (c < cmin) continue;
+                const float2 h = d.H32[row + (size_t)c * ld];
+                const double2 a = dots[c];
+                const float2 av = make_float2((float)a.x, (float)a.y);
+                acc.x = fmaf(h.x, av.x, fmaf(-h.y, av.y, acc.x));
+                acc.y = fmaf(h.x, av.y, fmaf(h.y, av.x, acc.y));
+            }
+        }
+        red[warp][lane] = acc;
+    }
+    // |a|^2 and a^dag b (same order in every CTA)
+    double aa = 0.0;
+    double2 ab = make_double2(0.0, 0.0);
+    for (int c = tid; c < p; c += SR_THREADS) {
+        const double2 av = dots[c], bv = dots[p + c];
+        aa += av.x * av.x + av.y * av.y;
+        ab.x += av.x * bv.x + av.y * bv.y;
+        ab.y += av.x * bv.y - av.y * bv.x;
+    }
+    aa = warp_sumd(aa);
+    ab.x = warp_sumd(ab.x);
+    ab.y = warp_sumd(ab.y);
+    if (lane == 0) {
+        sh_r[warp] = aa;
+        sh_c[warp] = ab;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double A2 = 0.0;
+        double2 AB = make_double2(0.0, 0.0);
+        for (int k = 0; k < SR_THREADS / 32; k++) {
+            A2 += sh_r[k];
+            AB.x += sh_c[k].x;
+            AB.y += sh_c[k].y;
+        }
+        const double guu = dots[2 * p].x;
+        double nu2 = guu - A2;
+        int stop = 0;
+        if (!(nu2 == nu2) || !(guu == guu)) {
+            stop = 2;  // NaN
+        } else if (nu2 <= 1e-24 * guu) {
+            stop = 1;  // invariant subspace reached (happy breakdown)
+            nu2 = 0.0;
+        }
+        const double nu = sqrt(nu2 > 0.0 ? nu2 : 0.0);
+        sh_nu = nu;
+        sh_stop = stop;
+        if (!stop) {
+            // q^dag w = (u^dag w - a^dag b)/nu, d_p = nu a_{p-1}, c_p = (q^dag w - d_p)/nu
+            const double inv = 1.0 / nu;
+            const double2 guw = dots[2 * p + 1];
+            const double2 qw = make_double2((guw.x - AB.x) * inv, (guw.y - AB.y) * inv);
+            const double2 al = dots[p - 1];
+            const double2 dp = make_double2(nu * al.x, nu * al.y);
+            const double2 cp = make_double2((qw.x - dp.x) * inv, (qw.y - dp.y) * inv);
+            sh_inv = inv;
+            sh_ep_r = dp.x * inv + cp.x;
+            sh_ep_i = dp.y * inv + cp.y;
+            if (blockIdx.x == 0) {
+                d.dvec[p] = dp;
+                d.H[p + (size_t)p * ld] = cp;
+                d.H32[p + (size_t)p * ld] = make_float2((float)cp.x, (float)cp.y);
+                d.scal[0] = inv;
+                d.scal[1] = -sh_ep_r * inv;
+                d.scal[2] = -sh_ep_i * inv;
+                d.scal[3] = nu;
+            }
+        }
+    }
+    __syncthreads();
+    const double nu = sh_nu;
+    const int stop = sh_stop;
+    if (warp == 0) {
+        const int c = r0 + lane;
+        float2 dr = red[0][lane];
+        for (int w = 1; w < SR_THREADS / 32; w++) {
+            dr.x += red[w][lane].x;
+            dr.y += red[w][lane].y;
+        }
+        if (c < p) {
+            const double2 av = dots[c];
+            // column p-1 += reorthogonalisation coefficients (on breakdown the
+            // accurate final pass does it with k_used = j - 1)
+            if (stop != 1) {
+                double2 h = d.H[c + (size_t)(p - 1) * ld];
+                h.x += av.x;
+                h.y += av.y;
+                d.H[c + (size_t)(p - 1) * ld] = h;
+                d.H32[c + (size_t)(p - 1) * ld] = make_float2((float)h.x, (float)h.y);
+            }
+            if (!stop) {
+                const double inv_nu = sh_inv, epr = sh_ep_r, epi = sh_ep_i;
+                const double2 bv = dots[p + c];
+                const double2 dv = make_double2(dr.x, dr.y);
+                d.dvec[c] = dv;
+                const double2 cc = make_double2((bv.x - dv.x) * inv_nu, (bv.y - dv.y) * inv_nu);
+                d.H[c + (size_t)p * ld] = cc;
+                d.H32[c + (size_t)p * ld] = make_float2((float)cc.x, (float)cc.y);
+                const double2 e = make_double2(dv.x * inv_nu + cc.x, dv.y * inv_nu + cc.y);
+                // g = e - (e_p/nu) a
+                const double2 g = make_double2(e.x - (epr * av.x - epi * av.y) * inv_nu,
+                                               e.y - (epr * av.y + epi * av.x) * inv_nu);
+                d.ap[c] = make_float2((float)(av.x * inv_nu), (float)(av.y * inv_nu));
+                const float2 sx = split_d(g.x), sy = split_d(g.y);
+                d.gh[c] = make_float2(sx.x, sy.x);
+                d.gl[c] = make_float2(sx.y, sy.y);
+            }
+        }
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        if (stop != 1) {
+            d.H[p + (size_t)(p - 1) * ld] = make_double2(nu, 0.0);
+            d.H32[p + (size_t)(p - 1) * ld] = make_float2((float)nu, 0.f);
+        }
+        if (stop) {
+            d.scal[4] = nu;
+            if (stop == 2) {
+                d.status = OVL_ENOCONV;
+                d.active = 0;
+            } else {
+                d.k_used = j - 1;  // the space spanned so far is invariant
+                d.active = 0;
+                d.fin = 1;         // u_j is in span(Q): the final pass projects it
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -731,10 +824,12 @@ int ovl_gs_reduce(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
 }
 
 int ovl_gs_small(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
-    // tiles of the largest solve (p <= pmax < OVL_MAXCOL)
-    const int ctmax = (b.pmax + SM_TC - 1) / SM_TC, trmax = (b.pmax + SM_TR - 1) / SM_TR;
-    dim3 grid(j == 1 || j < 0 ? 1 : ctmax * trmax, b.nsolve);
-    k_gs_small<<<grid, 256, 0, st>>>(b, j, ctmax > 0 ? ctmax : 1);
+    if (j == 1 || j < 0) {
+        k_gs_small<<<dim3(1, b.nsolve), 256, 0, st>>>(b, j);
+    } else {
+        // row tiles of the longest solve (p <= pmax < OVL_MAXCOL)
+        k_gs_small_rows<<<dim3((b.pmax + SR_ROWS - 1) / SR_ROWS, b.nsolve), SR_THREADS, 0, st>>>(b, j);
+    }
     OVL_LAUNCH_CHECK(lat);
     return OVL_OK;
 }

@@ -29,7 +29,6 @@ struct SolveDev {
     float2* H32;
     double2* dots;   // pass-A results: a[0..p), b[p..2p), g_uu, g_uw, g_ww
     double2* dvec;   // d = H a  (p+1)
-    float2* dpart;   // phase-1 partials of d: ceil(ldH/64) x ldH
     float2* ap;      // pass-B coefficients a/nu            (FP32)
     float2* gh;      // pass-B coefficients g, high part    (FP32)
     float2* gl;      // pass-B coefficients g, low part     (FP32)

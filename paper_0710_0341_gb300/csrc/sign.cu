@@ -206,7 +206,6 @@ struct SolvePlan {
     double2 *u = nullptr, *w = nullptr, *H = nullptr;
     float2* H32 = nullptr;
     double2 *dots = nullptr, *dvec = nullptr;
-    float2* dpart = nullptr;
     float2 *ap = nullptr, *gh = nullptr, *gl = nullptr;
     double* scal = nullptr;
     const float2** qhi = nullptr;
@@ -300,7 +299,6 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             t(p.H32, ld * ld);
             t(p.dots, 2 * ld + 3);
             t(p.dvec, ld + 1);
-            t(p.dpart, ((ld + 63) / 64) * ld);
             t(p.ap, ld);
             t(p.gh, ld);
             t(p.gl, ld);
@@ -439,7 +437,6 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         s.H32 = p.H32;
         s.dots = p.dots;
         s.dvec = p.dvec;
-        s.dpart = p.dpart;
         s.ap = p.ap;
         s.gh = p.gh;
         s.gl = p.gl;
