@@ -67,9 +67,12 @@ __global__ void __launch_bounds__(DOT_THREADS) k_gs_dot(BatchDev B, int j) {
     __shared__ double2 acc[2 * OVL_MAXCOL + 3];
     __shared__ const float2* s_col[OVL_MAXPTR];
     __shared__ float4 s_uw[DOTB_RB];  // (u.re, u.im, w.re, w.im) per row
+    __shared__ double s_sc[DOT_THREADS / 32][4];  // per-warp |u|^2, u^dag w, |w|^2 (summed in warp order)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nptr = d.nptr;
     for (int o = tid; o < 2 * p + 3; o += DOT_THREADS) acc[o] = make_double2(0.0, 0.0);
+    if (lane == 0)
+        for (int q = 0; q < 4; q++) s_sc[warp][q] = 0.0;
     for (int c = tid; c < nptr && c < p; c += DOT_THREADS) s_col[c] = d.qhi[c];
     const double2* __restrict__ u = d.u;
     const double2* __restrict__ w = d.w;
@@ -95,10 +98,10 @@ __global__ void __launch_bounds__(DOT_THREADS) k_gs_dot(BatchDev B, int j) {
             guwr = warp_sum(guwr);
             guwi = warp_sum(guwi);
             if (lane == 0) {
-                atomicAdd(&acc[2 * p].x, (double)guu);
-                atomicAdd(&acc[2 * p + 1].x, (double)guwr);
-                atomicAdd(&acc[2 * p + 1].y, (double)guwi);
-                atomicAdd(&acc[2 * p + 2].x, (double)gww);
+                s_sc[warp][0] += (double)guu;
+                s_sc[warp][1] += (double)guwr;
+                s_sc[warp][2] += (double)guwi;
+                s_sc[warp][3] += (double)gww;
             }
         }
         __syncthreads();
@@ -142,6 +145,15 @@ __global__ void __launch_bounds__(DOT_THREADS) k_gs_dot(BatchDev B, int j) {
                 acc[p + c].y += bi;
             }
         }
+    }
+    __syncthreads();
+    if (cg == 0 && tid == 0) {
+        double t[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < DOT_THREADS / 32; w++)
+            for (int q = 0; q < 4; q++) t[q] += s_sc[w][q];
+        acc[2 * p] = make_double2(t[0], 0.0);
+        acc[2 * p + 1] = make_double2(t[1], t[2]);
+        acc[2 * p + 2] = make_double2(t[3], 0.0);
     }
     __syncthreads();
     double2* out = B.part + ((size_t)s * B.G + blockIdx.x) * B.pstride;
@@ -635,7 +647,9 @@ __global__ void __launch_bounds__(256) k_proj_dot(ProjDev* pds, double2* part, i
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __shared__ double2 acc[OVL_MAXCOL + 1];
     __shared__ float4 s_x[PJ_RB];  // x split: (hi.re, hi.im, lo.re, lo.im)
+    __shared__ double s_nn[8];      // per-warp |x|^2 (summed in warp order)
     for (int o = tid; o <= d.ncol; o += 256) acc[o] = make_double2(0.0, 0.0);
+    if (lane == 0) s_nn[warp] = 0.0;
     for (size_t base = (size_t)blockIdx.x * PJ_RB; base < N; base += (size_t)gridDim.x * PJ_RB) {
         __syncthreads();  // acc zeroed / s_x reuse
         double nn = 0.0;
@@ -647,7 +661,7 @@ __global__ void __launch_bounds__(256) k_proj_dot(ProjDev* pds, double2* part, i
             nn += x.x * x.x + x.y * x.y;
         }
         nn = warp_sumd(nn);
-        if (lane == 0) atomicAdd(&acc[d.ncol].x, nn);
+        if (lane == 0) s_nn[warp] += nn;
         __syncthreads();
         const bool full = base + PJ_RB <= N;  // N is even: a float4 never straddles the end
         for (int c = warp; c < d.ncol; c += 8) {
@@ -683,6 +697,12 @@ __global__ void __launch_bounds__(256) k_proj_dot(ProjDev* pds, double2* part, i
                 acc[c].y += ai;
             }
         }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; w++) t += s_nn[w];
+        acc[d.ncol] = make_double2(t, 0.0);
     }
     __syncthreads();
     double2* out = part + ((size_t)s * G + blockIdx.x) * pstride;

@@ -13,6 +13,8 @@
 // chosen implicitly, no row swaps); the group meets at one barrier per pivot.
 // Barriers are counters in global memory with a bounded wait: a wait that
 // runs out sets OVL_ETIMEOUT for the solve and every CTA of the group leaves.
+#include <algorithm>
+
 #include "newton.cuh"
 #include "wait.cuh"
 
@@ -621,6 +623,7 @@ namespace {
 namespace cg = cooperative_groups;
 
 constexpr int NTC = 512;
+constexpr int GPF = 4;  // prefetched L2-row elements per thread and pivot
 
 // 1 / z for a complex df value: conj(z) * (1 / |z|^2), the real reciprocal
 // refined by one Newton step in df (error about 2^-46 relative)
@@ -649,7 +652,8 @@ __device__ __forceinline__ dfc dfc_inv(const dfc& z) {
 __device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
 __device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
-__global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve) {
+template <bool L2ROWS>
+__global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve, int nrs_max) {
     extern __shared__ float4 csm[];
     cg::cluster_group cl = cg::this_cluster();
     const int CL = (int)cl.num_blocks();
@@ -662,9 +666,15 @@ __global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nr = (n - g + CL - 1) / CL;            // own rows: i = g + CL * r
     const int nrmax = (n + CL - 1) / CL;
+    const int nrs = (L2ROWS && nrs_max < nrmax) ? nrs_max : nrmax;  // own rows kept in shared memory
     float4* X = (float4*)d.X;
-    float4* R = csm;                                 // nrmax x n
-    float4* crow = R + (size_t)nrmax * n;            // 2 x n candidate rows (read by the cluster)
+    float4* R = csm;                                 // nrs x n
+    // own rows nrs.. live in this CTA's private part of the work buffer (L2)
+    float4* Rg = d.Wg + (size_t)g * (size_t)(nrmax - nrs) * n;
+    auto rowp = [&](int r) -> float4* {
+        return (!L2ROWS || r < nrs) ? R + (size_t)r * n : Rg + (size_t)(r - nrs) * n;
+    };
+    float4* crow = R + (size_t)nrs * n;              // 2 x n candidate rows (read by the cluster)
     float4* prow = crow + 2 * (size_t)n;             // n: scaled pivot row
     float4* fcol = prow + n;                         // nrmax: column k of own rows
     int* piv = (int*)(fcol + ((nrmax + 1) & ~1));
@@ -697,7 +707,7 @@ __global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve
         int br = -1;
         for (int r = tid; r < nr; r += NTC) {
             if (used[g + CL * r]) continue;
-            const float4 v = R[(size_t)r * n + col];
+            const float4 v = rowp(r)[col];
             const float a = v.x * v.x + v.y * v.y;
             if (a > best) {
                 best = a;
@@ -728,7 +738,7 @@ __global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve
         if (br >= 0)
             for (int l = tid; l < n; l += NTC) {
                 row_update(br, l);
-                crow[(size_t)slot * n + l] = R[(size_t)br * n + l];
+                crow[(size_t)slot * n + l] = rowp(br)[l];
             }
         if (tid == 0) {
             c_val[slot] = br >= 0 ? best : -1.f;
@@ -741,7 +751,8 @@ __global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve
         iter++;
         for (int r = 0; r < nr; r++) {
             const int i = g + CL * r;
-            for (int l = tid; l < n; l += NTC) R[(size_t)r * n + l] = __ldcg(X + (size_t)i * n + l);
+            float4* rr = rowp(r);
+            for (int l = tid; l < n; l += NTC) rr[l] = __ldcg(X + (size_t)i * n + l);
         }
         for (int i = tid; i < n; i += NTC) used[i] = 0;
         if (tid == 0) {
@@ -800,15 +811,21 @@ __global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve
                 used[pr] = 1;
                 piv[k] = pr;
             }
-            for (int r = tid; r < nr; r += NTC) fcol[r] = R[(size_t)r * n + k];
+            for (int r = tid; r < nr; r += NTC) fcol[r] = rowp(r)[k];
             __syncthreads();
             const dfc inv = dfc_unpack(s_inv);
             for (int l = tid; l < n; l += NTC) prow[l] = l == k ? s_inv : dfc_pack(dfc_mul(dfc_unpack(pw[l]), inv));
             __syncthreads();
             const int rp = (pr % CL == g) ? (pr - g) / CL : -1;  // own index of the pivot row
             // x <- x - f p for own row r != rp at column l (column k: 0 - f p)
+            auto upd_val = [&](int r, int l, float4 xin) -> float4 {
+                if (r == rp) return prow[l];
+                const dfc pl = dfc_unpack(prow[l]);
+                const dfc f = dfc_unpack(fcol[r]);
+                return dfc_pack(dfc_fms(l == k ? dfc_zero() : dfc_unpack(xin), f, pl));
+            };
             auto upd = [&](int r, int l) {
-                float4* x = R + (size_t)r * n + l;
+                float4* x = rowp(r) + l;
                 if (r == rp) {
                     *x = prow[l];
                 } else {
@@ -826,16 +843,39 @@ __global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve
                 skip_l = k + 1;
                 cl_arrive();
             }
-            // every remaining (own row, column) pair once, flattened over the CTA
-            int r = tid / n, l = tid - (tid / n) * n;
-            const int total = nr * n;
-            for (int e = tid; e < total; e += NTC) {
-                if (r != skip_r && l != skip_l) upd(r, l);
-                l += NTC;
-                while (l >= n) {
-                    l -= n;
-                    r++;
+            // every remaining (own row, column) pair once, flattened over the
+            // CTA: the first GPF elements of the rows in L2 are loaded before the
+            // shared-memory rows are updated and written back after them
+            const int gtot = L2ROWS ? (nr > nrs ? nr - nrs : 0) * n : 0;
+            float4 gv[L2ROWS ? GPF : 1];
+#pragma unroll
+            for (int t = 0; t < (L2ROWS ? GPF : 0); t++) {
+                const int e = tid + t * NTC;
+                if (e < gtot) gv[t] = Rg[e];
+            }
+            {
+                int r = tid / n, l = tid - (tid / n) * n;
+                const int total = (nr < nrs ? nr : nrs) * n;
+                for (int e = tid; e < total; e += NTC) {
+                    if (r != skip_r && l != skip_l) upd(r, l);
+                    l += NTC;
+                    while (l >= n) {
+                        l -= n;
+                        r++;
+                    }
                 }
+            }
+#pragma unroll
+            for (int t = 0; t < (L2ROWS ? GPF : 0); t++) {
+                const int e = tid + t * NTC;
+                if (e < gtot) {
+                    const int r = nrs + e / n, l = e - (e / n) * n;
+                    if (r != skip_r && l != skip_l) Rg[e] = upd_val(r, l, gv[t]);
+                }
+            }
+            for (int e = tid + (L2ROWS ? GPF : 0) * NTC; e < gtot; e += NTC) {
+                const int r = nrs + e / n, l = e - (e / n) * n;
+                if (r != skip_r && l != skip_l) upd(r, l);
             }
             __syncthreads();
         }
@@ -853,7 +893,7 @@ __global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve
             for (int j = tid; j < n; j += NTC) {
                 const int l = piv[j];
                 const dfc xo = dfc_unpack(__ldcg(xr + l));  // rows of X move between CTAs
-                const dfc a = dfc_unpack(R[(size_t)r * n + j]);
+                const dfc a = dfc_unpack(rowp(r)[j]);
                 const dfc xn = dfc_axpby(0.5 * c, xo, 0.5 * ic, a);
                 const float dr = (xn.hi.x - xo.hi.x) + (xn.lo.x - xo.lo.x);
                 const float di = (xn.hi.y - xo.hi.y) + (xn.lo.y - xo.lo.y);
@@ -913,10 +953,11 @@ __global__ void __launch_bounds__(NTC, 1) k_newton_cl(NewtonDev* nds, int nsolve
     cl.sync();  // no CTA leaves while another may read its shared memory
 }
 
-size_t cl_smem_bytes(int n, int CL) {
+// shared memory of a CTA keeping nrs rows of an order-n matrix
+size_t cl_smem_bytes(int n, int CL, int nrs) {
     const size_t nrmax = (size_t)((n + CL - 1) / CL);
-    size_t b = nrmax * n * sizeof(float4);             // rows
-    b += 3 * (size_t)n * sizeof(float4);               // 2 candidate rows + pivot row
+    size_t b = (size_t)nrs * n * sizeof(float4);        // rows
+    b += 3 * (size_t)n * sizeof(float4);                // 2 candidate rows + pivot row
     b += (size_t)((nrmax + 1) & ~(size_t)1) * sizeof(float4);
     b += 2 * (size_t)n * sizeof(int) + (size_t)n + 64;
     return (b + 15) & ~(size_t)15;
@@ -924,31 +965,41 @@ size_t cl_smem_bytes(int n, int CL) {
 
 }  // namespace
 
-int ovl_newton_cl_plan(ovl_lattice lat, int nsolve, int nmax, int* cl_size, size_t* smem_out) {
-    // Cluster size: the rows must fit the cluster's shared memory, and a GPC
-    // hosts one cluster of 16 at most (a floor-swept GPC none), so a smaller
-    // cluster can keep every matrix of the batch resident in one wave. The
-    // cost of a size is waves x rows per CTA (the per-pivot work of a CTA).
+int ovl_newton_cl_plan(ovl_lattice lat, int nsolve, int nmax, int* cl_size, size_t* smem_out, int* nrs_out,
+                       int* l2rows_out) {
+    // Cluster size and rows per CTA in shared memory. A GPC hosts one cluster
+    // of 13..16 CTAs at most and a floor-swept GPC none, so a smaller cluster
+    // can keep every matrix of a batch resident in one wave; rows that do not
+    // fit a CTA's shared memory stay in its part of the work buffer (L2).
+    // Rows in L2 put their latency on the per-pivot path (measured: one wave
+    // of 12-CTA clusters with 7 of 36 rows in L2 is 1.4x slower than two
+    // waves of 16-CTA clusters with every row in shared memory at n = 430),
+    // so a shape with every row in shared memory is always preferred; among
+    // those, and among the others, the cost is waves x rows per CTA.
     *cl_size = 0;
     *smem_out = 0;
+    *nrs_out = 0;
+    *l2rows_out = 0;
     int optin = 0, dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return OVL_OK;
     const size_t avail = (size_t)optin - 1024;  // static shared memory of the kernel
-    if (cudaFuncSetAttribute((const void*)k_newton_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return OVL_OK;
-    }
-    if (cudaFuncSetAttribute((const void*)k_newton_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)avail) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return OVL_OK;
-    }
+    for (const void* fn : {(const void*)k_newton_cl<false>, (const void*)k_newton_cl<true>})
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)avail) != cudaSuccess) {
+            cudaGetLastError();
+            return OVL_OK;
+        }
     long best_cost = -1;
     for (int CL = 16; CL >= 2; CL--) {
-        const size_t smem = cl_smem_bytes(nmax, CL);
-        if (smem > avail) break;  // smaller clusters need more shared memory per CTA
+        const int nrmax = (nmax + CL - 1) / CL;
+        const size_t fixed = cl_smem_bytes(nmax, CL, 0);
+        if (fixed >= avail) continue;
+        const size_t fit = (avail - fixed) / ((size_t)nmax * sizeof(float4));
+        const int nrs = (int)std::min<size_t>((size_t)nrmax, fit);
+        const int ng = nrmax - nrs;
+        if (nrs < 1 || 2 * ng > nrmax) continue;
+        const size_t smem = cl_smem_bytes(nmax, CL, nrs);
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -961,26 +1012,30 @@ int ovl_newton_cl_plan(ovl_lattice lat, int nsolve, int nmax, int* cl_size, size
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int active = 0;
-        if (cudaOccupancyMaxActiveClusters(&active, (const void*)k_newton_cl, &cfg) != cudaSuccess) {
+        const void* fn = ng > 0 ? (const void*)k_newton_cl<true> : (const void*)k_newton_cl<false>;
+        if (cudaOccupancyMaxActiveClusters(&active, fn, &cfg) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
         if (active < 1) continue;
         const long waves = (nsolve + active - 1) / active;
-        const long cost = waves * (long)((nmax + CL - 1) / CL);
+        const long cost = (ng > 0 ? (1L << 40) : 0L) + waves * (long)(nrs + ng);
         if (best_cost < 0 || cost < best_cost) {
             best_cost = cost;
             *cl_size = CL;
             *smem_out = smem;
+            *nrs_out = nrs;
+            *l2rows_out = ng > 0 ? 1 : 0;
         }
     }
     (void)lat;
     return OVL_OK;
 }
 
-int ovl_newton_cl_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int cl_size, size_t smem, cudaStream_t st) {
-    OVL_CUDA_TRY(lat, cudaFuncSetAttribute((const void*)k_newton_cl, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
+int ovl_newton_cl_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int cl_size, size_t smem, int nrs,
+                         int l2rows, cudaStream_t st) {
+    const void* fn = l2rows ? (const void*)k_newton_cl<true> : (const void*)k_newton_cl<false>;
+    OVL_CUDA_TRY(lat, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -993,7 +1048,10 @@ int ovl_newton_cl_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int cl_
     cfg.stream = st;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    OVL_CUDA_TRY(lat, cudaLaunchKernelEx(&cfg, k_newton_cl, nd_dev, nsolve));
+    if (l2rows)
+        OVL_CUDA_TRY(lat, cudaLaunchKernelEx(&cfg, k_newton_cl<true>, nd_dev, nsolve, nrs));
+    else
+        OVL_CUDA_TRY(lat, cudaLaunchKernelEx(&cfg, k_newton_cl<false>, nd_dev, nsolve, nrs));
     lat->launches++;
     return OVL_OK;
 }

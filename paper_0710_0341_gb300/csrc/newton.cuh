@@ -65,7 +65,9 @@ int ovl_newton_df_plan(ovl_lattice lat, int nsolve, int nmax, int* cpm, int* sme
 int ovl_newton_df_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int nmax, int cpm, int smem_rows,
                          cudaStream_t st);
 // double-float Gauss-Jordan Newton, one thread-block cluster per matrix (rows in
-// the cluster's shared memory); cl_size 0 when no cluster shape fits n
-int ovl_newton_cl_plan(ovl_lattice lat, int nsolve, int nmax, int* cl_size, size_t* smem);
-int ovl_newton_cl_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int cl_size, size_t smem, cudaStream_t st);
+// the CTAs' shared memory, the rest of a CTA's rows in its part of Wg);
+// cl_size 0 when no cluster shape fits n
+int ovl_newton_cl_plan(ovl_lattice lat, int nsolve, int nmax, int* cl_size, size_t* smem, int* nrs, int* l2rows);
+int ovl_newton_cl_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int cl_size, size_t smem, int nrs,
+                         int l2rows, cudaStream_t st);
 int ovl_fmatvec_launch(ovl_lattice lat, NewtonDev* nd_dev, int nsolve, int nmax, cudaStream_t st);

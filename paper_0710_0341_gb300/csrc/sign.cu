@@ -659,13 +659,14 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             // cooperative) double-float only; 4: as 0 with every Newton-Schulz step
             // declined (the return to Gauss-Jordan)
             const int mode = params[0].newton_fp64;
-            int cl_size = 0, cpm_df = 1, smem_rows = 0;
+            int cl_size = 0, cl_nrs = 0, cl_l2 = 0, cpm_df = 1, smem_rows = 0;
             size_t cl_smem = 0;
-            if (mode == 0 || mode == 3 || mode == 4) ovl_newton_cl_plan(lat, nsolve, nmax_run, &cl_size, &cl_smem);
+            if (mode == 0 || mode == 3 || mode == 4)
+                ovl_newton_cl_plan(lat, nsolve, nmax_run, &cl_size, &cl_smem, &cl_nrs, &cl_l2);
             if (mode != 1 && cl_size == 0) ovl_newton_df_plan(lat, nsolve, nmax_run, &cpm_df, &smem_rows);
             auto launch_gj = [&]() -> int {
                 if (mode == 1) return ovl_newton_launch(lat, d_nd, nsolve, cpm_run, st);
-                if (cl_size > 0) return ovl_newton_cl_launch(lat, d_nd, nsolve, cl_size, cl_smem, st);
+                if (cl_size > 0) return ovl_newton_cl_launch(lat, d_nd, nsolve, cl_size, cl_smem, cl_nrs, cl_l2, st);
                 return ovl_newton_df_launch(lat, d_nd, nsolve, nmax_run, cpm_df, smem_rows, st);
             };
             if (int rc = launch_gj()) return rc;
