@@ -231,7 +231,7 @@ __device__ __forceinline__ void hop(const KArgs& a, const VT* __restrict__ in, s
 }
 
 template <typename T, typename VT, int LINKS>
-__global__ void __launch_bounds__(128) k_dslash(KArgs a) {
+__device__ __forceinline__ void dslash_site(const KArgs& a) {
     const int r = blockIdx.y;
     if (a.active && !a.active[(size_t)r * a.stride]) return;
     if (a.klim && a.j > a.klim[(size_t)r * a.stride]) return;
@@ -285,6 +285,19 @@ __global__ void __launch_bounds__(128) k_dslash(KArgs a) {
     store_spinor<T, VT>(out, a.V, site, o);
 }
 
+// FP64 spinors: the compiler's register choice (142 for FP64 links, no spills)
+template <typename T, typename VT, int LINKS>
+__global__ void __launch_bounds__(128) k_dslash(KArgs a) {
+    dslash_site<T, VT, LINKS>(a);
+}
+
+// FP32 spinors: at most 64 registers, 8 CTAs per SM (measured 13 % faster
+// than 96 registers with 12-real links at 24^3x48, in spite of a few spills)
+template <typename T, typename VT, int LINKS>
+__global__ void __launch_bounds__(128, 8) k_dslash32(KArgs a) {
+    dslash_site<T, VT, LINKS>(a);
+}
+
 }  // namespace
 
 int ovl_dslash_launch(ovl_lattice lat, const DslashArgs& d, int fmt, int links, cudaStream_t st) {
@@ -319,9 +332,9 @@ int ovl_dslash_launch(ovl_lattice lat, const DslashArgs& d, int fmt, int links, 
         if (links == OVL_LINKS_F64)
             return ovl_fail(lat, OVL_ENOTSUP, "F32 spinors with F64 links are not built");
         else if (links == OVL_LINKS_F32)
-            k_dslash<float, float2, OVL_LINKS_F32><<<grid, 128, 0, st>>>(a);
+            k_dslash32<float, float2, OVL_LINKS_F32><<<grid, 128, 0, st>>>(a);
         else
-            k_dslash<float, float2, OVL_LINKS_R12><<<grid, 128, 0, st>>>(a);
+            k_dslash32<float, float2, OVL_LINKS_R12><<<grid, 128, 0, st>>>(a);
     }
     OVL_LAUNCH_CHECK(lat);
     return OVL_OK;

@@ -279,3 +279,55 @@ def test_newton_kernels_large_projected_matrix(ks):
                 assert rel(ys[mode][i], ys[1][i]) < 1e-11, (k, mode, rel(ys[mode][i], ys[1][i]))
     finally:
         ovl.ovl_destroy_lattice(h)
+
+
+def test_source_in_invariant_subspace():
+    """b a combination of three eigenvectors of H_w: the Krylov space is
+    3-dimensional (Sec. 2), so any k >= 3 gives sgn(A) b exactly (Eqs. 4-6)."""
+    need_gpu()
+    mu, m_w = 0.3, -1.0
+    U, A = _setup(DIMS, 0.5, mu, m_w)
+    lam, Vr = np.linalg.eig(A.toarray())
+    idx = [i for i in np.argsort(-np.abs(lam.real)) if abs(lam[i].real) > 0.05][:3]
+    coef = np.array([1.0, 2.0, 0.5])
+    b = (Vr[:, idx] @ coef).reshape(synth.lattice_shape(DIMS) + (4, 3))
+    ystar = (Vr[:, idx] @ (coef * np.sign(lam[idx].real))).reshape(b.shape)
+    h = lattice(DIMS, U)
+    try:
+        for k in (3, 12):
+            y = np.zeros_like(b)
+            info = ovl.ovl_sign_apply(h, [dict(mu=mu, m_w=m_w, k=k)], [None], b, y)
+            assert info[0]["status"] == 0
+            assert rel(y, ystar) < 1e-10, (k, rel(y, ystar))
+    finally:
+        ovl.ovl_destroy_lattice(h)
+
+
+def test_source_in_deflated_subspace():
+    """b inside span(S) (Schur) or span(R) (LR): the projected remainder x is at
+    the rounding level, y comes from the deflated part alone (Eqs. 16, 22) and
+    equals sgn(A) b."""
+    need_gpu()
+    mu, m_w = 0.3, -1.0
+    U, A = _setup(DIMS, 0.5, mu, m_w)
+    S, T, lam, R, L = _schur(A, DIMS, 12)
+    Ad = A.toarray()
+    rng = np.random.default_rng(5)
+    c = rng.standard_normal(12) + 1j * rng.standard_normal(12)
+    shape = synth.lattice_shape(DIMS) + (4, 3)
+    bs = (S @ c).reshape(shape)
+    bl = (R @ c).reshape(shape)
+    ys = matfunc.sign_eig_apply(Ad, bs.ravel()).reshape(shape)
+    yl = (R @ (np.sign(lam.real) * c)).reshape(shape)
+    h = lattice(DIMS, U)
+    try:
+        ds = _defl_schur(h, mu, m_w, S, T, DIMS)
+        dl = _defl_lr(h, mu, m_w, lam, R, L, DIMS)
+        y = np.zeros((2,) + shape, complex)
+        infos = ovl.ovl_sign_apply(h, [dict(mu=mu, m_w=m_w, k=10)] * 2, [ds, dl], np.stack([bs, bl]), y)
+        assert all(i["status"] == 0 for i in infos)
+        assert infos[0]["beta"] < 1e-10 * np.linalg.norm(bs) and infos[1]["beta"] < 1e-10 * np.linalg.norm(bl)
+        assert rel(y[0], ys) < 1e-10, rel(y[0], ys)
+        assert rel(y[1], yl) < 1e-10, rel(y[1], yl)
+    finally:
+        ovl.ovl_destroy_lattice(h)
