@@ -75,7 +75,7 @@ typedef struct {
     int    newton_fp64;      /* 0 (default): double-float Gauss-Jordan Newton (one thread-block
                               * cluster per matrix when its rows fit the cluster's shared memory,
                               * else the cooperative kernel), finished by Newton-Schulz steps
-                              * once a step is below 1e-2 and |I - X^2|_F < 1/2;
+                              * once a step is below 3e-2 and |I - X^2|_F < 1/2;
                               * 1: FP64 Gauss-Jordan Newton; 2: double-float Gauss-Jordan Newton,
                               * cooperative kernel only; 3: as 0 without Newton-Schulz;
                               * 4: as 0 with every Newton-Schulz step declined, so that the

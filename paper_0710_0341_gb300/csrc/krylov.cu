@@ -16,6 +16,7 @@
 // of pass A only need FP32 products (they steer orthogonality), while pass B
 // accumulates in double-float (48 bits) against the stored hi+lo basis.
 #include <algorithm>
+#include <cmath>
 
 #include "df.cuh"
 #include "krylov.cuh"
@@ -823,12 +824,27 @@ int ovl_gs_grid(ovl_lattice lat) {
 }
 
 int ovl_gs_dot(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
-    // column groups: about eight CTAs per SM (measured: 3 % faster than two
-    // per SM at 8^4, 8 solves; u and w are re-staged per group from L2)
-    int cgs = (8 * lat->num_sms + b.G * b.nsolve - 1) / (b.G * b.nsolve);
-    if (cgs < 1) cgs = 1;
-    if (cgs > 8) cgs = 8;
-    if (b.pmax < 8 * cgs) cgs = std::max(1, b.pmax / 8);
+    // Column groups: the grid G x nsolve x CG should fill whole waves of
+    // resident CTAs (measured at 8^4, 8 solves: CG = 3, 1.89 waves, 5.34 TB/s;
+    // CG = 4, 2.53 waves, 4.89 TB/s); among CG = 1..8 take the largest
+    // waves / ceil(waves), ties to fewer groups (less staging of u, w).
+    static int occ = 0;
+    if (!occ) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gs_dot, DOT_THREADS, 0);
+        if (occ < 1) occ = 1;
+    }
+    const double slots = (double)occ * lat->num_sms;
+    int cgs = 1;
+    double best = -1.0;
+    for (int cg = 1; cg <= 8; cg++) {
+        if (cg > 1 && b.pmax < 8 * cg) break;  // at least 8 columns per group
+        const double w = (double)b.G * b.nsolve * cg / slots;
+        const double eff = w / std::ceil(w);
+        if (eff > best + 0.01) {
+            best = eff;
+            cgs = cg;
+        }
+    }
     dim3 grid(b.G, b.nsolve, cgs);
     k_gs_dot<<<grid, DOT_THREADS, 0, st>>>(b, j);
     OVL_LAUNCH_CHECK(lat);

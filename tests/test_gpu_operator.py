@@ -36,6 +36,26 @@ def test_apply_hw_fp64_and_fp32(dims, apbc, mu):
         ovl.ovl_destroy_lattice(h)
 
 
+@pytest.mark.parametrize("nrhs", [1, 10])
+def test_apply_hw_fp64_8x4_multi_rhs(nrhs):
+    """8^4, FP64 spinors and links, one and ten right-hand sides (the bench's
+    lattice; up to 40960 site applications per launch): equal to the oracle's
+    Eq. 2 to 1e-13."""
+    need_gpu()
+    dims = (8, 8, 8, 8)
+    U = synth.random_su3_field(dims, 0.4, 0)
+    h = lattice(dims, U)
+    try:
+        A = dirac.hermitian_wilson(U, 0.3, -1.0)
+        x = np.stack([synth.gaussian_source(dims, 10 + i) for i in range(nrhs)])
+        ref = np.stack([dirac.apply(A, xi) for xi in x])
+        out = np.zeros_like(x)
+        ovl.ovl_apply_Hw(h, 0.3, -1.0, x, out, nrhs, ovl.OVL_LINKS_F64)
+        assert rel(out, ref) < 1e-13, rel(out, ref)
+    finally:
+        ovl.ovl_destroy_lattice(h)
+
+
 def test_packed_roundtrip_and_packed_stencil():
     torch = need_gpu()
     dims = (4, 6, 2, 4)
