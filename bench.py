@@ -38,7 +38,7 @@ METRIC = "sgn(H_w(mu)) b solves/s at 1e-8 rel err vs FP64 oracle"
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
 # over the launches of one timed step) from the ncu launch list of this
 # command, profiles/bench_launches_8x4.md; valid while the kernel is unchanged.
-NCU_TRAFFIC = {"gs_pass_b": 1.3725e9, "gs_pass_a": 0.7131e9}
+NCU_TRAFFIC = {"gs_pass_b": 1.3725e9, "gs_pass_a": 0.7032e9}
 WORKLOAD = "8^4 eps=0.4 m_w=-1 mu={0,0.1,0.3,0.6} x {Schur,LR} k=400 m=30, FP64 mode"
 
 

@@ -147,8 +147,8 @@ __global__ void __launch_bounds__(NS_THREADS) k_ns_gemm(const NsDev* __restrict_
     }
 }
 
-// per matrix: region test, step, convergence (the Gauss-Jordan kernels' rule);
-// tile partials summed in tile order
+// per matrix: region test, step, convergence (the Gauss-Jordan kernels' rule,
+// plus: stop once a step is <= 1e-8); tile partials summed in tile order
 __global__ void k_ns_check(NsDev* nds, int nsolve, int max_iter, int tn) {
     const int t2 = tn * tn;
     for (int s = threadIdx.x; s < nsolve; s += blockDim.x) {
@@ -172,7 +172,9 @@ __global__ void k_ns_check(NsDev* nds, int nsolve, int max_iter, int tn) {
             if (!(rel == rel)) {
                 d.fallback = 1;
                 d.on = 0;
-            } else if (rel <= d.tol || d.prev <= 1e-10 || (d.prev < 1e-8 && rel > 0.5 * d.prev)) {
+            } else if (rel <= d.tol || rel <= 1e-8 || d.prev <= 1e-10 || (d.prev < 1e-8 && rel > 0.5 * d.prev)) {
+                // rel <= 1e-8: the step is quadratic, so the new iterate's error is
+                // about rel^2, at the rounding level of the double-float products
                 d.done = 1;
                 d.on = 0;
             } else if (d.iters >= max_iter) {
