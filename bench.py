@@ -266,6 +266,29 @@ def main():
     breakdown = {c: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                      "GB_per_s": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 and v["bytes"] > 0 else None}
                  for c, v in prof.items()}
+    # ---- overlap operator D_ov = 1 + gamma5 sgn(H_w) and its adjoint (Eq. 1) on
+    # the LR half of the workload (adjoint deflation data by swapping L and R) ----
+    ovl_meas = None
+    if rank == 0:
+        lr = [d for d, su in zip(defl, setup) if su["scheme"] == "lr"]
+        adj = [ovl.ovl_deflation_adjoint(d) for d in lr]
+        pl = [dict(mu=mu, m_w=MW, k=K_KRYLOV, prec=ovl.OVL_PREC_FP64) for mu in MUS]
+        xo = bd[:4].clone()
+        yo = torch.zeros_like(xo)
+        res = {}
+        for name, dd, adjf in (("D_ov", lr, False), ("D_ov_dagger", adj, True)):
+            ovl.ovl_overlap_apply(h, pl, dd, xo, yo, adjoint=adjf)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ovl.ovl_overlap_apply(h, pl, dd, xo, yo, adjoint=adjf)
+            e1.record()
+            torch.cuda.synchronize()
+            ms_ov = e0.elapsed_time(e1)
+            res[name] = {"ms_per_call": ms_ov, "applications_per_s": 4 / (ms_ov / 1e3)}
+        for d in adj:
+            ovl.ovl_destroy_deflation(d)
+        ovl_meas = dict(res, config="4 solves (LR, mu in {0,0.1,0.3,0.6}), k=400, m=30, FP64 mode, one call each")
     # ---- stencil GB/s at 24^3x48 (12-real links, FP32, single rhs, > L2) ----
     sten = None
     if rank == 0:
@@ -288,7 +311,7 @@ def main():
                 "accuracy": {"rel_err_est_per_solve": acc, "meets_1e-8": ok,
                              "reference": "tests/golden/config2_ystar_sketch.json (oracle)"},
                 "newton_iters": [i["newton_iters"] for i in infos],
-                "kernel_breakdown": breakdown, "stencil": sten,
+                "kernel_breakdown": breakdown, "stencil": sten, "overlap_operator": ovl_meas,
                 "deflation_setup": {"total_s": setup_s, "per_operator": setup}}
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -192,6 +192,27 @@ int ovl_destroy_deflation(ovl_deflation d);
 int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params* params,
                    const ovl_deflation* defl, const double* b, double* y, ovl_sign_info* info);
 
+/* ---- the overlap operator (Sec. 1, Eq. 1) -------------------------------
+ * adjoint = 0: y_i = D_ov(mu_i) x_i = x_i + gamma_5 sgn(H_w(mu_i)) x_i.
+ * adjoint = 1: y_i = D_ov(mu_i)^dag x_i = x_i + sgn(H_w(-mu_i)) gamma_5 x_i
+ *              (sgn(H_w(mu))^dag = sgn(H_w(-mu)), from Eq. 2); params keep
+ *              mu_i, and defl[i] must belong to H_w(-mu_i) (NULL, or from
+ *              ovl_deflation_adjoint).
+ * The sign runs as in ovl_sign_apply with the same params (info as there);
+ * x, y: nsolve canonical spinors, host or device; gamma_5 = diag(1,1,-1,-1) on
+ * the spin index. Allocates 3 x nsolve spinors of device work space per call.
+ * Errors as ovl_sign_apply; OVL_EINVAL for adjoint not 0 or 1. */
+int ovl_overlap_apply(ovl_lattice lat, int nsolve, const ovl_sign_params* params,
+                      const ovl_deflation* defl, const double* x, double* y, int adjoint,
+                      ovl_sign_info* info);
+
+/* LR deflation data of H_w(-mu) = H_w(mu)^dag from those of H_w(mu) (Eq. 20:
+ * left and right eigenvectors swap, eigenvalues are conjugated), for the
+ * adjoint overlap operator with one eigenvector computation (Sec. 5). The new
+ * object is owned by the caller (ovl_destroy_deflation). OVL_ENOTSUP for
+ * Schur data (the Schur vectors of H_w(mu) are not those of its adjoint). */
+int ovl_deflation_adjoint(ovl_deflation d, ovl_deflation* out);
+
 /* ---- learned (k, m) predictor (not in the paper) ---------------------- */
 
 /* A small MLP x (n_in) -> ReLU -> ReLU -> y (n_out), FP32 on the device, with

@@ -19,6 +19,8 @@ Modules and what they restate:
                   as an independent second route for the tests.
 * ``freefield``-- the closed-form sign of H_w(mu) on the free field U = 1 in
                   momentum space (derived from Eq. 2).
+* ``overlap``  -- the overlap operator D_ov(mu) = 1 + gamma5 sgn(H_w(mu)) of
+                  Eq. 1 and its adjoint via sgn(H_w(-mu)); LR data of the adjoint.
 * ``krylov``   -- Arnoldi (Eq. 7) with classical Gram-Schmidt plus one
                   reorthogonalisation, the approximation of Eq. 11, the Schur
                   deflation of Eqs. 13-19 (with the Sylvester equation, Eq. 18),

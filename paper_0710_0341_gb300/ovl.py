@@ -57,6 +57,9 @@ _SIGS = {
     "ovl_deflation_stats": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "ovl_sign_apply": (C.c_int, [_P, C.c_int, C.POINTER(ovl_sign_params), C.POINTER(_P), _P, _P,
                                  C.POINTER(ovl_sign_info)]),
+    "ovl_overlap_apply": (C.c_int, [_P, C.c_int, C.POINTER(ovl_sign_params), C.POINTER(_P), _P, _P, C.c_int,
+                                    C.POINTER(ovl_sign_info)]),
+    "ovl_deflation_adjoint": (C.c_int, [_P, C.POINTER(_P)]),
     "ovl_launch_count": (C.c_int, [_P, C.POINTER(C.c_longlong)]),
     "ovl_mlp_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(_P)]),
     "ovl_mlp_destroy": (C.c_int, [_P]),
@@ -222,6 +225,42 @@ def ovl_sign_apply(h, params, defl, b, y, info=True):
         err.infos = infos
         raise err
     return infos
+
+
+def ovl_overlap_apply(h, params, defl, x, y, adjoint=False):
+    """D_ov(mu) x (adjoint=False) or D_ov(mu)^dag x (True) per solve; params and
+    defl as in ovl_sign_apply (for the adjoint: deflation data of H_w(-mu))."""
+    n = len(params)
+    P = (ovl_sign_params * n)()
+    for i, p in enumerate(params):
+        P[i].mu = p["mu"]
+        P[i].m_w = p["m_w"]
+        P[i].k = int(p["k"])
+        P[i].prec = int(p.get("prec", OVL_PREC_FP64))
+        P[i].newton_max_iter = int(p.get("newton_max_iter", 0))
+        P[i].newton_tol = float(p.get("newton_tol", 0.0))
+        P[i].newton_fp64 = int(p.get("newton_fp64", 0))
+        P[i].adapt_every = int(p.get("adapt_every", 0))
+        P[i].k_max = int(p.get("k_max", 0))
+        P[i].tol = float(p.get("tol", 0.0))
+    D = (_P * n)(*[(d.value if isinstance(d, _P) else d) if d is not None else None for d in (defl or [None] * n)])
+    I = (ovl_sign_info * n)()
+    rc = lib().ovl_overlap_apply(h, n, P, D, _ptr(x), _ptr(y), int(bool(adjoint)), I)
+    infos = [dict(status=I[i].status, k_used=I[i].k_used, m_used=I[i].m_used, newton_iters=I[i].newton_iters,
+                  beta=I[i].beta, beta_k=I[i].beta_k, err_est=I[i].err_est) for i in range(n)]
+    if rc != OVL_OK:
+        msg = lib().ovl_last_error(h)
+        err = OvlError(rc, (msg.decode() if msg else "") + f" infos={infos}")
+        err.infos = infos
+        raise err
+    return infos
+
+
+def ovl_deflation_adjoint(d):
+    """LR deflation data of H_w(-mu) from those of H_w(mu) (new handle)."""
+    out = _P()
+    _check(lib().ovl_deflation_adjoint(d, C.byref(out)))
+    return out
 
 
 def ovl_launch_count(h):
