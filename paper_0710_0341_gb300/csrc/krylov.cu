@@ -667,7 +667,9 @@ __global__ void __launch_bounds__(256) k_proj_dot(ProjDev* pds, double2* part, i
         const bool full = base + PJ_RB <= N;  // N is even: a float4 never straddles the end
         for (int c = warp; c < d.ncol; c += 8) {
             const float4* __restrict__ qh = (const float4*)d.qhi[c] + (base >> 1);
-            const float4* __restrict__ ql = d.qlo ? (const float4*)d.qlo[c] + (base >> 1) : nullptr;
+            // columns without a low plane (FP32 basis) have a null entry: offset only real planes
+            const float2* const qlc = d.qlo ? d.qlo[c] : nullptr;
+            const float4* __restrict__ ql = qlc ? (const float4*)qlc + (base >> 1) : nullptr;
             dfacc a;
             dfacc_zero(a);
 #pragma unroll
@@ -751,7 +753,10 @@ __global__ void __launch_bounds__(256) k_proj_update(ProjDev* pds, size_t N) {
     for (size_t r = blockIdx.x * (size_t)256 + threadIdx.x; r < N; r += (size_t)gridDim.x * 256) {
         dfacc acc;
         dfacc_zero(acc);
-        for (int c = 0; c < d.ncol; c++) dfacc_mac(acc, d.qhi[c][r], d.qlo[c][r], gh[c], gl[c]);
+        for (int c = 0; c < d.ncol; c++) {
+            const float2* lp = d.qlo ? d.qlo[c] : nullptr;  // null: column without a low plane
+            dfacc_mac(acc, d.qhi[c][r], lp ? lp[r] : make_float2(0.f, 0.f), gh[c], gl[c]);
+        }
         double2 v = dfacc_value(acc);
         double2 x = d.x[r];
         d.x[r] = make_double2(x.x - v.x, x.y - v.y);

@@ -122,6 +122,26 @@ def test_uneven_batch_mixed_schemes():
         ovl.ovl_destroy_lattice(h)
 
 
+@pytest.mark.parametrize("prec", [ovl.OVL_PREC_MIXED, ovl.OVL_PREC_MIXED_R12])
+def test_mixed_precision_several_row_blocks(prec):
+    """4^4 (N = 3072: the projection kernels run several 1024-row blocks over
+    Krylov columns that have no low plane): the mixed modes agree with the FP64
+    mode to their FP32 bound."""
+    need_gpu()
+    dims, mu, m_w = (4, 4, 4, 4), 0.3, -1.0
+    U = synth.random_su3_field(dims, 0.5, 0)
+    b = synth.gaussian_source(dims, 1)
+    h = lattice(dims, U)
+    try:
+        y64 = np.zeros_like(b)
+        ym = np.zeros_like(b)
+        ovl.ovl_sign_apply(h, [dict(mu=mu, m_w=m_w, k=120)], [None], b, y64)
+        ovl.ovl_sign_apply(h, [dict(mu=mu, m_w=m_w, k=120, prec=prec)], [None], b, ym)
+        assert rel(ym, y64) < 1e-5, rel(ym, y64)
+    finally:
+        ovl.ovl_destroy_lattice(h)
+
+
 @pytest.mark.parametrize("prec,tol", [(ovl.OVL_PREC_MIXED, 1e-5), (ovl.OVL_PREC_MIXED_R12, 1e-5)])
 def test_mixed_precision_bound(prec, tol):
     need_gpu()
