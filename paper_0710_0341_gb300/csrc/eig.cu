@@ -102,7 +102,6 @@ class Solver {
     float2 *H32, *ap, *gh, *gl;
     double* scal;
     const float2 **qhi, **qlo;
-    int* counters;
     SolveDev* d_sd;
     ProjDev* d_pd;
     GemvDev* d_gd;
@@ -142,7 +141,6 @@ class Solver {
         G = ovl_gs_grid(lat);
         pstride = 2 * (int)ld + 3;
         TRYP(part = mem.get<double2>((size_t)std::max(G * pstride, G * (int)(ld + 1) * 1) * (size_t)std::max(1, nev)));
-        TRYP(counters = mem.get<int>(4));
         TRYP(d_sd = mem.get<SolveDev>(1));
         TRYP(d_pd = mem.get<ProjDev>(ld));
         TRYP(d_gd = mem.get<GemvDev>(ld));
@@ -152,7 +150,6 @@ class Solver {
         TRYP(d_mu = mem.get<double>(2));
         TRYP(Vf = mem.get<double2>(N * (size_t)nev));
         TRYP(Wf = mem.get<double2>(N * (size_t)nev));
-        OVL_CUDA_TRY(lat, cudaMemsetAsync(counters, 0, 4 * sizeof(int), st));
         void* hp[4] = {u, tmp, tmp, w};
         OVL_CUDA_TRY(lat, cudaMemcpyAsync(dsl, hp, sizeof hp, cudaMemcpyHostToDevice, st));
         OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_mu, &mu, sizeof(double), cudaMemcpyHostToDevice, st));
@@ -302,7 +299,6 @@ class Solver {
             bd.part = part;
             bd.G = G;
             bd.pstride = pstride;
-            bd.counters = counters;
             bd.df = 1;
             if (first) {
                 // v_1 = x/|x| into column 0

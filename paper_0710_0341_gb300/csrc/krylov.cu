@@ -313,7 +313,6 @@ __global__ void __launch_bounds__(256) k_gs_small(BatchDev B, int j) {
                 d.fin = 0;
             }
         }
-        if (!final_pass && tid == 0) B.counters[s] = 0;
         return;
     }
     // coefficients of column p (rows 0..p-1) and of pass B
@@ -334,7 +333,6 @@ __global__ void __launch_bounds__(256) k_gs_small(BatchDev B, int j) {
         d.gh[c] = make_float2(sx.x, sy.x);
         d.gl[c] = make_float2(sx.y, sy.y);
     }
-    if (tid == 0) B.counters[s] = 0;
 }
 
 // Small step for j >= 2, one CTA per 32 rows r of the tile [r0, r0 + 32):

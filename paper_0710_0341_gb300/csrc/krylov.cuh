@@ -49,7 +49,6 @@ struct BatchDev {
     double2* part;   // partial sums: nsolve x G x pstride
     int G;           // CTAs per solve of the streaming passes
     int pstride;     // >= 2*OVL_MAXCOL + 3
-    int* counters;   // nsolve ints (last-block detection), zero between launches
     int pmax;        // max over solves of the basis columns used at this step
     int df;          // FP64 mode: basis has low planes
 };

@@ -23,11 +23,6 @@ namespace {
 constexpr int NT = 256;
 constexpr long long SPIN_LIMIT = 1ll << 24;  // polls of ~100 ns: about 2 s
 
-struct Group {
-    NewtonDev* nd;
-    int s, g, cpm;
-};
-
 // Barrier for the CTAs of one solve (group_wait in wait.cuh, bounded).
 __device__ __forceinline__ bool group_sync(NewtonDev& d, unsigned& gen, int cpm) {
     return group_wait(d.bar, d.status, gen, cpm, SPIN_LIMIT);

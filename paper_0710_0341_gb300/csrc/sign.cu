@@ -279,7 +279,6 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     }
     const int G = ovl_gs_grid(lat);
     const int pstride = std::max(2 * ldmax + 3, mdef_max + 1);
-    const int cpm = ovl_newton_cpm(lat, nsolve, ldmax);
     // ---- sizes and one allocation ----
     auto plan_bytes = [&](bool carve, char* base) -> size_t {
         Carve c{base};
@@ -346,7 +345,6 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         ProjDev* pd = nullptr;
         GemvDev* gd = nullptr;
         double2* part = nullptr;
-        int* counters = nullptr;
         double* mu = nullptr;
         void** ptrs = nullptr;
         double2* canon = nullptr;  // canonical staging for host b / y
@@ -362,7 +360,6 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         q.pd = cb.take<ProjDev>(nsolve);
         q.gd = cb.take<GemvDev>(nsolve);
         q.part = cb.take<double2>((size_t)nsolve * G * pstride);
-        q.counters = cb.take<int>(nsolve);
         q.mu = cb.take<double>(nsolve);
         q.ptrs = cb.take<void*>(2 * (size_t)nsolve);
         q.canon = cb.take<double2>(N * nsolve);
@@ -391,7 +388,6 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     ProjDev* d_pd = bp.pd;
     GemvDev* d_gd = bp.gd;
     double2* d_part = bp.part;
-    int* d_counters = bp.counters;
     double* d_mu = bp.mu;
     void** d_ptrs = bp.ptrs;
     double2* d_canon = bp.canon;
@@ -405,7 +401,6 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     }
     for (int i = 0; i < nsolve; i++)
         if (int rc = ovl_pack_impl(lat, bsrc + 2 * N * i, P[i].u, 1, OVL_VEC_F64, st)) return rc;
-    OVL_CUDA_TRY(lat, cudaMemsetAsync(d_counters, 0, nsolve * sizeof(int), st));
 
     // ---- column pointers, descriptors ----
     std::vector<SolveDev> hs(nsolve);
@@ -538,7 +533,6 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     bd.part = d_part;
     bd.G = G;
     bd.pstride = pstride;
-    bd.counters = d_counters;
     bd.df = df;
     bd.pmax = 0;
     // beta^2 sits in .x of pout3[0]; pass it through a per-solve array
@@ -652,7 +646,6 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_nd, nd.data(), nsolve * sizeof(NewtonDev), cudaMemcpyHostToDevice, st));
         if (any_run) {
             int cpm_run = ovl_newton_cpm(lat, nsolve, nmax_run);
-            (void)cpm;
             ProfScope pn(lat, 5, 0.0, st);
             // 0: cluster (else cooperative) double-float Gauss-Jordan, Newton-Schulz finish;
             // 1: FP64 Gauss-Jordan; 2: cooperative double-float only; 3: cluster (else
