@@ -239,6 +239,10 @@ def test_sign_argument_errors():
             ovl.ovl_sign_apply(h, [dict(mu=0.3, m_w=-1.0, k=5), dict(mu=0.3, m_w=-1.0, k=5, prec=1)],
                                [None, None], np.stack([b, b]), np.zeros((2,) + b.shape, complex))
         assert e.value.code == ovl.OVL_EINVAL
+        for bad in (dict(k=0), dict(m_w=-4.0), dict(newton_fp64=7), dict(prec=9)):
+            with pytest.raises(ovl.OvlError) as e:  # depth < 1, kappa infinite, unknown modes
+                ovl.ovl_sign_apply(h, [dict(dict(mu=0.3, m_w=-1.0, k=5), **bad)], [None], b, y)
+            assert e.value.code == ovl.OVL_EINVAL, bad
     finally:
         ovl.ovl_destroy_lattice(h)
 
