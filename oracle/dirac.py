@@ -120,6 +120,43 @@ def hermitian_wilson(U: np.ndarray, mu: float, m_w: float, antiperiodic_t: bool 
     return (gamma5_matrix(V) @ wilson_dirac(U, mu, m_w, antiperiodic_t)).tocsr()
 
 
+def hermitian_wilson_rows(U: np.ndarray, mu: float, m_w: float, psi: np.ndarray, sites,
+                          antiperiodic_t: bool = False) -> np.ndarray:
+    """(H_w(mu) psi) at the given sites only (Eq. 2, then gamma_5), by plain
+    loops over the eight hops: for lattices whose sparse matrix is too large to
+    build. psi and U in the canonical shapes; returns (len(sites), 4, 3)."""
+    lt, lz, ly, lx = U.shape[:4]
+    dims = (lx, ly, lz, lt)
+    kap = kappa_of(m_w)
+    out = []
+    for site in sites:
+        x = site % lx
+        y = (site // lx) % ly
+        z = (site // (lx * ly)) % lz
+        t = site // (lx * ly * lz)
+        c = [x, y, z, t]
+        acc = np.zeros((4, 3), dtype=np.complex128)
+        for nu in range(4):
+            for fwd in (True, False):
+                cn = list(c)
+                cn[nu] = (c[nu] + (1 if fwd else -1)) % dims[nu]
+                sign = 1.0
+                if nu == 3 and antiperiodic_t and ((fwd and c[3] == lt - 1) or (not fwd and c[3] == 0)):
+                    sign = -1.0
+                w = (np.exp(mu) if fwd else np.exp(-mu)) if nu == 3 else 1.0
+                nb = psi[cn[3], cn[2], cn[1], cn[0]]  # (4, 3)
+                if fwd:
+                    link = U[t, z, y, x, nu]
+                    proj = np.eye(4) + GAMMA[nu]
+                else:
+                    link = np.conj(U[cn[3], cn[2], cn[1], cn[0], nu]).T
+                    proj = np.eye(4) - GAMMA[nu]
+                acc += sign * w * (proj @ nb @ link.T)
+        d = psi[t, z, y, x] - kap * acc
+        out.append(GAMMA5 @ d)
+    return np.array(out)
+
+
 def apply(A, psi: np.ndarray) -> np.ndarray:
     """A @ psi for a canonical-shaped spinor (keeps the shape)."""
     return (A @ psi.reshape(-1)).reshape(psi.shape)

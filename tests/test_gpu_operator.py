@@ -106,3 +106,30 @@ def test_invalid_arguments_are_rejected():
             ovl.ovl_apply_Hw(h, 0.1, -1.0, x, np.zeros_like(x), 1, 7)
     finally:
         ovl.ovl_destroy_lattice(h)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dims,eps,m_w", [((16, 16, 16, 32), 0.3, -1.2), ((24, 24, 24, 48), 0.3, -1.0)])
+def test_apply_hw_full_size_sampled(dims, eps, m_w):
+    """Full lattice sizes of the 16^3x32 and 24^3x48 workloads, one right-hand
+    side (the stencil launch the bench times): H_w x at 48 sampled sites
+    (corners, faces, random) against the oracle's row evaluation of Eq. 2;
+    FP64 links 1e-13, FP32 and 12-real links 2e-6 of the largest entry."""
+    need_gpu()
+    U = synth.random_su3_field(dims, eps, 0)
+    x = synth.gaussian_source(dims, 1)
+    V = int(np.prod(dims))
+    rng = np.random.default_rng(0)
+    sites = sorted({0, V - 1, dims[0] - 1, V - dims[0], V // 2, dims[0] * dims[1] * dims[2]}
+                   | {int(v) for v in rng.integers(0, V, 42)})
+    ref = dirac.hermitian_wilson_rows(U, 0.2, m_w, x, sites)
+    h = lattice(dims, U)
+    try:
+        for links, tol in ((ovl.OVL_LINKS_F64, 1e-13), (ovl.OVL_LINKS_F32, 2e-6), (ovl.OVL_LINKS_R12, 2e-6)):
+            out = np.zeros_like(x)
+            ovl.ovl_apply_Hw(h, 0.2, m_w, x, out, 1, links)
+            got = out.reshape(-1, 4, 3)[sites]
+            err = np.abs(got - ref).max() / np.abs(ref).max()
+            assert err < tol, (links, err)
+    finally:
+        ovl.ovl_destroy_lattice(h)
