@@ -355,3 +355,30 @@ def test_source_in_deflated_subspace():
         assert rel(y[1], yl) < 1e-10, rel(y[1], yl)
     finally:
         ovl.ovl_destroy_lattice(h)
+
+
+@pytest.mark.slow
+def test_uneven_batch_full_size_12x4():
+    """The 12^4 lattice of the 48-solve workload (N = 248832), uneven depths
+    and chemical potentials in one batch: each solve equals the same solve run
+    alone (the per-solve arithmetic and its reduction order do not depend on the
+    batch), and at mu = 0 sgn(H_w) is a unitary involution, so the Krylov
+    result's norm approaches |b| as its estimate converges."""
+    need_gpu()
+    dims, m_w = (12, 12, 12, 12), -1.0
+    U = synth.random_su3_field(dims, 0.4, 0)
+    b = synth.gaussian_source(dims, 1)
+    h = lattice(dims, U)
+    try:
+        params = [dict(mu=0.05, m_w=m_w, k=150), dict(mu=0.2, m_w=m_w, k=220), dict(mu=0.8, m_w=m_w, k=300),
+                  dict(mu=0.0, m_w=m_w, k=300)]
+        yb = np.zeros((4,) + b.shape, complex)
+        infos = ovl.ovl_sign_apply(h, params, [None] * 4, np.stack([b] * 4), yb)
+        assert [i["k_used"] for i in infos] == [150, 220, 300, 300]
+        for i, p in enumerate(params[:3]):
+            y1 = np.zeros_like(b)
+            ovl.ovl_sign_apply(h, [p], [None], b, y1)
+            assert rel(yb[i], y1) <= 1e-14, (i, rel(yb[i], y1))
+        assert abs(np.linalg.norm(yb[3]) / np.linalg.norm(b) - 1.0) < 1e-2
+    finally:
+        ovl.ovl_destroy_lattice(h)
