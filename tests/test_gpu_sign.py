@@ -362,8 +362,8 @@ def test_uneven_batch_full_size_12x4():
     """The 12^4 lattice of the 48-solve workload (N = 248832), uneven depths
     and chemical potentials in one batch: each solve equals the same solve run
     alone (the per-solve arithmetic and its reduction order do not depend on the
-    batch), and at mu = 0 sgn(H_w) is a unitary involution, so the Krylov
-    result's norm approaches |b| as its estimate converges."""
+    batch). At mu = 0 H_w is Hermitian, so <b, y> = beta^2 e_1^dag sgn(H_k) e_1 is
+    real for the approximation itself, and |y| is near |b| (sgn(H_w) is unitary)."""
     need_gpu()
     dims, m_w = (12, 12, 12, 12), -1.0
     U = synth.random_su3_field(dims, 0.4, 0)
@@ -379,6 +379,8 @@ def test_uneven_batch_full_size_12x4():
             y1 = np.zeros_like(b)
             ovl.ovl_sign_apply(h, [p], [None], b, y1)
             assert rel(yb[i], y1) <= 1e-14, (i, rel(yb[i], y1))
-        assert abs(np.linalg.norm(yb[3]) / np.linalg.norm(b) - 1.0) < 1e-2
+        ip = np.vdot(b.ravel(), yb[3].ravel())
+        assert abs(ip.imag) <= 1e-10 * np.linalg.norm(b) ** 2, ip
+        assert 0.5 < np.linalg.norm(yb[3]) / np.linalg.norm(b) < 1.5
     finally:
         ovl.ovl_destroy_lattice(h)
