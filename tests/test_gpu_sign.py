@@ -380,7 +380,7 @@ def test_uneven_batch_full_size_12x4():
             ovl.ovl_sign_apply(h, [p], [None], b, y1)
             assert rel(yb[i], y1) <= 1e-14, (i, rel(yb[i], y1))
         ip = np.vdot(b.ravel(), yb[3].ravel())
-        assert abs(ip.imag) <= 1e-10 * np.linalg.norm(b) ** 2, ip
+        assert abs(ip.imag) <= 1e-8 * np.linalg.norm(b) ** 2, ip
         assert 0.5 < np.linalg.norm(yb[3]) / np.linalg.norm(b) < 1.5
     finally:
         ovl.ovl_destroy_lattice(h)
