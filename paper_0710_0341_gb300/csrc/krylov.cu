@@ -5,7 +5,8 @@
 // "delayed" variant: step j makes two passes over the basis Q_p (p = m + j - 1
 // final columns) instead of four:
 //   pass A (k_gs_dot):    a = Q_p^dag u_j,  b = Q_p^dag w    (w = A u_j)
-//   small  (k_gs_small):  nu = sqrt(|u_j|^2 - |a|^2); q_{p+1} = (u_j - Q_p a)/nu
+//   small  (k_gs_small_rows; k_gs_small for the first step and the final pass):
+//                         nu = sqrt(|u_j|^2 - |a|^2); q_{p+1} = (u_j - Q_p a)/nu
 //                         is the reorthogonalised, normalised column; the
 //                         coefficients c of A q_{p+1} on Q_{p+1} follow from
 //                         a, b and d = H a without touching Q again

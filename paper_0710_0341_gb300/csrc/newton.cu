@@ -7,8 +7,15 @@
 // fell below 1e-10 (quadratic convergence puts the next one near rounding),
 // or when rounding stalls it (the step below 1e-8 no longer halves).
 //
-// One cooperative launch runs every iteration of every solve of a batch. The
-// CTAs of one solve form a group that owns the matrix rows round-robin and
+// Three implementations of the iteration live here: the FP64 kernel (below,
+// newton_fp64 = 1), the double-float cooperative kernel (the fallback when no
+// cluster shape fits), and the double-float kernel on thread-block clusters
+// (the default; its comment block further down describes it). By default the
+// iteration hands over to the Newton-Schulz finish of newton_schulz.cu once
+// a step is below a threshold.
+//
+// FP64 kernel: one cooperative launch runs every iteration of every solve of
+// a batch. The CTAs of one solve form a group that owns the matrix rows round-robin and
 // inverts X_i by Gauss-Jordan elimination with partial pivoting (pivot rows
 // chosen implicitly, no row swaps); the group meets at one barrier per pivot.
 // Barriers are counters in global memory with a bounded wait: a wait that
