@@ -233,22 +233,30 @@ __device__ __forceinline__ void hop(const KArgs& a, const VT* __restrict__ in, s
 template <typename T, typename VT, int LINKS>
 __device__ __forceinline__ void dslash_site(const KArgs& a) {
     const int r = blockIdx.y;
-    if (a.active && !a.active[(size_t)r * a.stride]) return;
+    if (a.active && !a.active[(size_t)r * a.stride]) return;  // whole CTA (one right-hand side)
     if (a.klim && a.j > a.klim[(size_t)r * a.stride]) return;
+    // e^{+-mu} of this right-hand side, once per CTA: an FP64 exp per thread
+    // kept the FP64 pipe half busy in the FP32 kernel
+    __shared__ T s_w[2];
+    if (threadIdx.x == 0) {
+        const double mu = a.mu[r];
+        s_w[0] = (T)exp(mu);
+        s_w[1] = (T)exp(-mu);
+    }
+    __syncthreads();
     const size_t site = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (site >= a.V) return;
     const VT* __restrict__ in = (const VT*)a.in[r];
     VT* __restrict__ out = (VT*)a.out[r];
-    const double mu = a.mu[r];
     const int Lx = a.Lx, Ly = a.Ly, Lz = a.Lz, Lt = a.Lt;
     const size_t sy = Lx, sz = (size_t)Lx * Ly, st = sz * Lz;
-    size_t q = site;
-    const int x = (int)(q % Lx);
-    q /= Lx;
-    const int y = (int)(q % Ly);
-    q /= Ly;
-    const int z = (int)(q % Lz);
-    const int t = (int)(q / Lz);
+    unsigned q = (unsigned)site;  // V < 2^31 (checked when the lattice is created)
+    const int x = (int)(q % (unsigned)Lx);
+    q /= (unsigned)Lx;
+    const int y = (int)(q % (unsigned)Ly);
+    q /= (unsigned)Ly;
+    const int z = (int)(q % (unsigned)Lz);
+    const int t = (int)(q / (unsigned)Lz);
     const size_t xp = x + 1 == Lx ? site - (Lx - 1) : site + 1;
     const size_t xm = x == 0 ? site + (Lx - 1) : site - 1;
     const size_t yp = y + 1 == Ly ? site - (Ly - 1) * sy : site + sy;
@@ -257,7 +265,7 @@ __device__ __forceinline__ void dslash_site(const KArgs& a) {
     const size_t zm = z == 0 ? site + (Lz - 1) * sz : site - sz;
     const size_t tp = t + 1 == Lt ? site - (Lt - 1) * st : site + st;
     const size_t tm = t == 0 ? site + (Lt - 1) * st : site - st;
-    T wtp = (T)exp(mu), wtm = (T)exp(-mu);
+    T wtp = s_w[0], wtm = s_w[1];
     if (a.apbc) {
         if (t + 1 == Lt) wtp = -wtp;
         if (t == 0) wtm = -wtm;
