@@ -1,0 +1,84 @@
+"""Host logic of bench.py, on the CPU with stand-ins for the library and for
+torch's device calls (the GPU measurement itself runs only on a GPU)."""
+import numpy as np
+
+import bench
+
+
+def test_clock_summary_reads_median_max_and_reasons():
+    row = lambda mhz, hw="Not Active", cap="Not Active": [  # noqa: E731
+        "0", str(mhz), "2070", "900.5", "0x0", hw, "Not Active", "Not Active", cap]
+    s = bench.clock_summary([row(2070), row(1980, cap="Active"), row(2055), ["0", "[N/A]"]])
+    assert s["sm_mhz"] == 2055 and s["sm_max_mhz"] == 2070 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    s = bench.clock_summary([row(1500, hw="Active")])
+    assert s["reasons"] == ["hw_slowdown"]
+    assert bench.clock_summary([]) == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+class _Event:
+    t = 0.0
+
+    def __init__(self, enable_timing=True):
+        self.at = None
+
+    def record(self):
+        _Event.t += 50.0  # 50 ms between consecutive records
+        self.at = _Event.t
+
+    def elapsed_time(self, other):
+        return other.at - self.at
+
+
+class _Cuda:
+    Event = _Event
+
+    @staticmethod
+    def synchronize():
+        pass
+
+
+class _Tensor:
+    def __init__(self, a):
+        self.a = a
+
+    def cpu(self):
+        return self
+
+    def numpy(self):
+        return self.a
+
+
+class _Torch:
+    cuda = _Cuda
+
+    @staticmethod
+    def zeros_like(t):
+        return _Tensor(np.zeros_like(t.a))
+
+
+class _Lib:
+    OVL_PREC_FP64, OVL_PREC_MIXED, OVL_PREC_MIXED_R12 = 0, 1, 2
+
+    def __init__(self):
+        self.calls = []
+
+    def ovl_sign_apply(self, h, params, defl, b, y):
+        self.calls.append([p["prec"] for p in params])
+        y.a[:] = b.a
+
+
+def test_mixed_modes_times_both_modes_on_the_batch(monkeypatch):
+    errs = {1: [5e-8] * 8, 2: [7e-8] * 7 + [2e-7]}
+    lib = _Lib()
+    monkeypatch.setattr(bench, "reference_sketch", lambda: {"0.0": {}})
+    monkeypatch.setattr(bench, "accuracy", lambda y, sk: errs[lib.calls[-1][0]])
+    bd = _Tensor(np.ones((8, 4), complex))
+    out = bench.mixed_modes(_Torch, lib, None, [None] * 8, bd, 3)
+    # one warm-up and three timed calls per mode, each over the 8-solve batch in one precision
+    assert [c[0] for c in lib.calls] == [1] * 4 + [2] * 4
+    assert all(len(set(c)) == 1 and len(c) == 8 for c in lib.calls)
+    a, b = out["fp32_basis_fp32_links"], out["fp32_basis_r12_links"]
+    assert abs(a["ms_per_step"] - 50.0 / 3) < 1e-9
+    assert abs(a["solves_per_s"] - 8 / (50.0 / 3 / 1e3)) < 1e-6
+    assert a["meets_1e-8"] is False and b["rel_err_est_per_solve"][-1] == 2e-7
