@@ -469,19 +469,21 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             q.coef = q.out;
             maxcol = std::max(maxcol, q.ncol);
         }
-        if (int rc = cudaMemcpyAsync(d_pd, pd.data(), nsolve * sizeof(ProjDev), cudaMemcpyHostToDevice, st))
-            return ovl_fail(lat, OVL_ECUDA, "copy failed (%d)", rc);
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_pd, pd.data(), nsolve * sizeof(ProjDev), cudaMemcpyHostToDevice, st));
         if (int rc = ovl_proj_dot(lat, d_pd, nsolve, maxcol, d_part, G, st)) return rc;
-        if (which == 2 || maxcol == 0) return cudaStreamSynchronize(st) == cudaSuccess ? OVL_OK : OVL_ECUDA;
+        if (which == 2 || maxcol == 0) {
+            OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
+            return OVL_OK;
+        }
         // update x -= Q coef with the update columns (S for Schur, R for LR)
         for (int i = 0; i < nsolve; i++) {
             pd[i].qhi = P[i].pu_hi;
             pd[i].qlo = P[i].pu_lo;
         }
-        if (int rc = cudaMemcpyAsync(d_pd, pd.data(), nsolve * sizeof(ProjDev), cudaMemcpyHostToDevice, st))
-            return ovl_fail(lat, OVL_ECUDA, "copy failed (%d)", rc);
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_pd, pd.data(), nsolve * sizeof(ProjDev), cudaMemcpyHostToDevice, st));
         if (int rc = ovl_proj_update(lat, d_pd, nsolve, maxcol, st)) return rc;
-        return cudaStreamSynchronize(st) == cudaSuccess ? OVL_OK : OVL_ECUDA;
+        OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
+        return OVL_OK;
     };
     for (int i = 0; i < nsolve; i++) {
         SolvePlan& p = P[i];
