@@ -378,32 +378,41 @@ def replica_throughput(ms_local, units_local, ws, device):
 
 
 def stencil_gbs(torch, ovl, synth):
-    dims = (24, 24, 24, 48)
-    V = 24 * 24 * 24 * 48
-    h2 = ovl.ovl_create_lattice(dims, 0, None)
-    ovl.ovl_set_links(h2, torch.from_numpy(synth.random_su3_field(dims, 0.3, 0)).cuda())
+    """Stencil-only launches on packed spinors at sizes above L2: 24^3x48 with
+    one right-hand side (three link formats) and 16^3x32 with 12 right-hand
+    sides in one launch. Algorithmic bytes per launch: spinors in and out per
+    right-hand side plus the four links of each site once."""
+    cases = (((24, 24, 24, 48), 1, (("fp32_r12", 1, 2, 8, 48), ("fp32_18", 1, 1, 8, 72), ("fp64", 0, 0, 16, 144))),
+             ((16, 16, 16, 32), 12, (("fp32_r12_16x3x32_12rhs", 1, 2, 8, 48),)))
     res = {}
-    for name, fmt, links, sb, lb in (("fp32_r12", 1, 2, 8, 48), ("fp32_18", 1, 1, 8, 72), ("fp64", 0, 0, 16, 144)):
-        x = torch.randn(12 * V, dtype=torch.complex64 if fmt == 1 else torch.complex128, device="cuda")
-        o = torch.zeros_like(x)
-        for _ in range(3):
-            ovl.ovl_apply_Hw_packed(h2, [0.3], MW, x, o, 1, fmt, links)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ovl.ovl_profile(h2, 1)
-        e0.record()
-        n = 20
-        for _ in range(n):
-            ovl.ovl_apply_Hw_packed(h2, [0.3], MW, x, o, 1, fmt, links)
-        e1.record()
-        torch.cuda.synchronize()
-        pr = ovl.ovl_profile(h2, 0)["stencil"]
-        dt = pr["ms"] / pr["launches"] / 1e3  # kernel-only (events around each launch)
-        byt = V * (2 * 12 * sb + 4 * lb)
-        res[name] = {"us_per_launch": dt * 1e6, "GB_per_s": byt / dt / 1e9, "bytes_per_site": 2 * 12 * sb + 4 * lb,
-                     "call_us_incl_host": e0.elapsed_time(e1) / n * 1e3}
-    ovl.ovl_destroy_lattice(h2)
-    res["lattice"] = "24^3x48, 1 rhs, packed, call-level CUDA events (includes launch)"
+    for dims, nrhs, fmts in cases:
+        V = int(np.prod(dims))
+        h2 = ovl.ovl_create_lattice(dims, 0, None)
+        ovl.ovl_set_links(h2, torch.from_numpy(synth.random_su3_field(dims, 0.3, 0)).cuda())
+        mus = [0.3] * nrhs
+        for name, fmt, links, sb, lb in fmts:
+            x = torch.randn(12 * V * nrhs, dtype=torch.complex64 if fmt == 1 else torch.complex128, device="cuda")
+            o = torch.zeros_like(x)
+            for _ in range(3):
+                ovl.ovl_apply_Hw_packed(h2, mus, MW, x, o, nrhs, fmt, links)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ovl.ovl_profile(h2, 1)
+            e0.record()
+            n = 20
+            for _ in range(n):
+                ovl.ovl_apply_Hw_packed(h2, mus, MW, x, o, nrhs, fmt, links)
+            e1.record()
+            torch.cuda.synchronize()
+            pr = ovl.ovl_profile(h2, 0)["stencil"]
+            dt = pr["ms"] / pr["launches"] / 1e3  # kernel-only (events around each launch)
+            byt = V * (nrhs * 2 * 12 * sb + 4 * lb)
+            res[name] = {"us_per_launch": dt * 1e6, "GB_per_s": byt / dt / 1e9, "rhs": nrhs,
+                         "bytes_per_site": byt / V, "call_us_incl_host": e0.elapsed_time(e1) / n * 1e3}
+            del x, o
+        ovl.ovl_destroy_lattice(h2)
+    res["lattice"] = ("24^3x48 with 1 rhs, 16^3x32 with 12 rhs (links counted once per launch); packed; "
+                      "kernel time from the library's events around each launch")
     return res
 
 

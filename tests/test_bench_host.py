@@ -82,3 +82,83 @@ def test_mixed_modes_times_both_modes_on_the_batch(monkeypatch):
     assert abs(a["ms_per_step"] - 50.0 / 3) < 1e-9
     assert abs(a["solves_per_s"] - 8 / (50.0 / 3 / 1e3)) < 1e-6
     assert a["meets_1e-8"] is False and b["rel_err_est_per_solve"][-1] == 2e-7
+
+
+class _Buf:
+    def __init__(self, n, dtype):
+        self.n, self.dtype = n, dtype
+
+    def cuda(self):
+        return self
+
+
+class _Torch2(_Torch):
+    complex64, complex128 = "c64", "c128"
+
+    @staticmethod
+    def from_numpy(a):
+        return _Buf(a.size, a.dtype)
+
+    @staticmethod
+    def randn(n, dtype=None, device=None):
+        return _Buf(n, dtype)
+
+    @staticmethod
+    def zeros_like(t):
+        return _Buf(t.n, t.dtype)
+
+
+class _StencilLib:
+    """Stand-in whose stencil takes 10 us per launch and records each call."""
+
+    def __init__(self):
+        self.calls, self.lat = [], {}
+        self.on = False
+        self.launches = 0
+
+    def ovl_create_lattice(self, dims, apbc, stream):
+        h = len(self.lat) + 1
+        self.lat[h] = dims
+        return h
+
+    def ovl_set_links(self, h, U):
+        pass
+
+    def ovl_destroy_lattice(self, h):
+        del self.lat[h]
+
+    def ovl_apply_Hw_packed(self, h, mus, m_w, x, o, nrhs, fmt, links):
+        V = int(np.prod(self.lat[h]))
+        assert x.n == o.n == 12 * V * nrhs and len(mus) == nrhs
+        assert x.dtype == ("c64" if fmt == 1 else "c128")
+        self.calls.append((self.lat[h], nrhs, fmt, links))
+        self.launches += self.on
+
+    def ovl_profile(self, h, enable):
+        self.on = bool(enable)
+        if enable:
+            self.launches = 0
+            return None
+        return {"stencil": {"ms": 0.01 * self.launches, "launches": self.launches}}
+
+
+class _Synth:
+    @staticmethod
+    def random_su3_field(dims, eps, seed):
+        return np.zeros(1)
+
+
+def test_stencil_cases_count_spinors_per_rhs_and_links_once():
+    lib = _StencilLib()
+    res = bench.stencil_gbs(_Torch2, lib, _Synth)
+    assert not lib.lat  # every lattice destroyed
+    V24, V16 = 24 ** 3 * 48, 16 ** 3 * 32
+    expect = {"fp32_r12": (V24, 1, 2 * 12 * 8 + 4 * 48), "fp32_18": (V24, 1, 2 * 12 * 8 + 4 * 72),
+              "fp64": (V24, 1, 2 * 12 * 16 + 4 * 144), "fp32_r12_16x3x32_12rhs": (V16, 12, 12 * 2 * 12 * 8 + 4 * 48)}
+    for name, (V, nrhs, bps) in expect.items():
+        r = res[name]
+        assert r["rhs"] == nrhs and r["bytes_per_site"] == bps
+        assert abs(r["us_per_launch"] - 10.0) < 1e-9
+        assert abs(r["GB_per_s"] - V * bps / 10e-6 / 1e9) < 1e-6 * r["GB_per_s"]
+    # 3 warm-up and 20 timed launches per case, the 12-rhs case in one launch each
+    assert len(lib.calls) == 4 * 23 and lib.calls[-1] == ((16, 16, 16, 32), 12, 1, 2)
