@@ -162,3 +162,9 @@ def test_stencil_cases_count_spinors_per_rhs_and_links_once():
         assert abs(r["GB_per_s"] - V * bps / 10e-6 / 1e9) < 1e-6 * r["GB_per_s"]
     # 3 warm-up and 20 timed launches per case, the 12-rhs case in one launch each
     assert len(lib.calls) == 4 * 23 and lib.calls[-1] == ((16, 16, 16, 32), 12, 1, 2)
+
+
+def test_amortised_throughput_includes_the_setup():
+    a = bench.amortised(100.0, 250.0, 8)
+    assert abs(a["1_sources_per_operator"] - 8 / 100.25) < 1e-12
+    assert abs(a["12_sources_per_operator"] - 96 / 103.0) < 1e-12
