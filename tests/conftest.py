@@ -11,3 +11,28 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: takes more than a few seconds on the CPU")
+    spec = os.environ.get("ORACLE_MUTANT")
+    if spec:
+        _plant_oracle_mutant(spec)
+
+
+def _plant_oracle_mutant(spec):
+    """Swap one oracle module's functions and constants for those of a copy of
+    its source with one textual change planted in it. Only the child pytest
+    processes of test_oracle_mutants.py set ORACLE_MUTANT; the oracle files
+    themselves are never modified."""
+    import importlib
+    import inspect
+    import json
+
+    s = json.loads(spec)
+    mod = importlib.import_module(s["module"])
+    src = inspect.getsource(mod)
+    if src.count(s["old"]) != 1:
+        raise pytest.UsageError(f"mutation target occurs {src.count(s['old'])} times in {s['module']}")
+    ns = {"__name__": mod.__name__, "__package__": mod.__package__, "__spec__": mod.__spec__,
+          "__file__": mod.__file__}
+    exec(compile(src.replace(s["old"], s["new"]), mod.__file__, "exec"), ns)
+    for k, v in ns.items():
+        if not k.startswith("__"):
+            setattr(mod, k, v)
