@@ -832,12 +832,12 @@ int ovl_gs_dot(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
     // resident CTAs (measured at 8^4, 8 solves: CG = 3, 1.89 waves, 5.34 TB/s;
     // CG = 4, 2.53 waves, 4.89 TB/s); among CG = 1..8 take the largest
     // waves / ceil(waves), ties to fewer groups (less staging of u, w).
-    static int occ = 0;
-    if (!occ) {
+    if (!lat->gs_dot_occ) {
+        int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gs_dot, DOT_THREADS, 0);
-        if (occ < 1) occ = 1;
+        lat->gs_dot_occ = occ < 1 ? 1 : occ;
     }
-    const double slots = (double)occ * lat->num_sms;
+    const double slots = (double)lat->gs_dot_occ * lat->num_sms;
     int cgs = 1;
     double best = -1.0;
     for (int cg = 1; cg <= 8; cg++) {
@@ -881,11 +881,12 @@ int ovl_gs_update(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
     dim3 grid((unsigned)g, b.nsolve);
     // the batch is homogeneous in precision (checked by the caller)
     size_t dyn = (size_t)b.pmax * 3 * sizeof(float2) + 2 * OVL_MAXPTR * sizeof(void*);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_gs_update<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-        cudaFuncSetAttribute(k_gs_update<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-        attr_set = true;
+    if (!lat->gs_update_attr) {  // a function attribute of the lattice's device
+        OVL_CUDA_TRY(lat, cudaFuncSetAttribute(k_gs_update<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               64 * 1024));
+        OVL_CUDA_TRY(lat, cudaFuncSetAttribute(k_gs_update<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               64 * 1024));
+        lat->gs_update_attr = true;
     }
     if (b.df)
         k_gs_update<true><<<grid, 256, dyn, st>>>(b, j);

@@ -57,6 +57,9 @@ struct ovl_lattice_s {
     void* ws = nullptr;
     size_t ws_bytes = 0;
     int num_sms = 0;
+    // per-device launch facts of this lattice's device, found on first use
+    int gs_dot_occ = 0;            // resident pass-A CTAs per SM
+    bool gs_update_attr = false;   // pass B may take more than 48 KB of shared memory
     // kernels launched by this handle, and optional per-class event timing
     long long launches = 0;
     bool prof = false;
