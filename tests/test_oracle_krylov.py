@@ -130,3 +130,23 @@ def test_eigenvector_input_basis_invariance(small):
     y1 = krylov.sign_schur_block(A, b, 25, S, T)
     y2 = krylov.sign_schur_block(A, b, 25, S2, T2)
     assert rel(y1, y2) < 1e-12
+
+
+def test_sparse_critical_pairs_match_the_dense_route(small):
+    """ARPACK on A^2 with Rayleigh-Ritz (the sparse route for lattices too
+    large for a dense decomposition) finds the same critical eigenvalues as the
+    dense eigendecomposition, eigenvectors spanning the same space, and left
+    vectors from H_w(-mu) with L^dag R = I."""
+    U = synth.random_su3_field((2, 2, 2, 4), 0.5, 0)
+    Am = dirac.hermitian_wilson(U, -0.3, -1.0)
+    m = 12
+    lam, R, L, res = eigen.critical_sparse(small["A"], Am, m, nev=24)
+    assert np.abs(lam - small["lam"][:m]).max() < 1e-10
+    assert res.max() < 1e-10 * np.abs(small["Ad"]).max()
+    # same span: the dense eigenvectors lie in span(R)
+    Qr, _ = np.linalg.qr(R)
+    Rd = small["R"][:, :m]
+    assert np.linalg.norm(Rd - Qr @ (Qr.conj().T @ Rd)) < 1e-9
+    assert np.abs(L.conj().T @ R - np.eye(m)).max() < 1e-9
+    # left vectors: L^dag A = Lambda L^dag
+    assert np.linalg.norm(L.conj().T @ small["Ad"] - lam[:, None] * L.conj().T) < 1e-9 * np.linalg.norm(L)

@@ -74,6 +74,10 @@ CASES = [
     ("critical = smallest Re instead of |Re|", "oracle.eigen",
      "np.abs(lam.imag), np.abs(lam.real)))", "np.abs(lam.imag), lam.real))", [KRY]),
     ("Schur block without the conjugate", "oracle.eigen", "T0 = Q.conj().T @ AQ", "T0 = Q.T @ AQ", [KRY]),
+    ("left vectors paired with lambda instead of conj(lambda)", "oracle.eigen",
+     "np.abs(lamL - np.conj(z))", "np.abs(lamL - z)", [KRY]),
+    ("Rayleigh-Ritz without the conjugate", "oracle.eigen",
+     "lam, Y = np.linalg.eig(Q.conj().T @ AQ)", "lam, Y = np.linalg.eig(Q.T @ AQ)", [KRY]),
     # Eq. 1, the overlap operator
     ("gamma5 = diag(-1, -1, 1, 1)", "oracle.overlap", "y[..., 2:, :] *= -1.0", "y[..., :2, :] *= -1.0", [OVL]),
     ("adjoint with gamma5 on the wrong side", "oracle.overlap",
