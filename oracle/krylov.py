@@ -21,6 +21,9 @@ sign is independent of the Newton iteration the CUDA path uses.
 * ``sign_lr``          -- Eqs. 20-22: R f(Lambda) L^dag x + beta V_k f(H_k) e_1
                           on x_minus = x - R L^dag x.
 * ``sign_hermitian_deflated`` -- Eq. 12 (orthonormal eigenvectors).
+* ``lr_search_space``, ``best_approximation`` -- span(R_m) + K_k(A, x_minus)
+                          and the orthogonal projection of the exact result
+                          on a space (the comparison of Sec. 5).
 """
 from __future__ import annotations
 
@@ -140,6 +143,14 @@ def sign_hermitian_deflated(A, x: np.ndarray, k: int, U: np.ndarray, lam: np.nda
     r = arnoldi(A, x_perp, k)
     F = f(r["H"])
     return U @ (np.sign(np.asarray(lam).real) * c) + r["beta"] * (r["V"] @ F[:, 0])
+
+
+def lr_search_space(A, x: np.ndarray, k: int, R: np.ndarray, L: np.ndarray) -> np.ndarray:
+    """Basis of the space the LR approximation of Eq. 22 lies in: span(R_m)
+    plus the Krylov space K_k(A, x_minus) of x_minus = x - R L^dag x (Eq. 21)."""
+    x = np.asarray(x, dtype=np.complex128).ravel()
+    x_minus = x - R @ (L.conj().T @ x)
+    return np.concatenate([R, arnoldi(A, x_minus, k)["V"]], axis=1)
 
 
 def best_approximation(Q: np.ndarray, y_exact: np.ndarray) -> np.ndarray:

@@ -150,3 +150,19 @@ def test_sparse_critical_pairs_match_the_dense_route(small):
     assert np.abs(L.conj().T @ R - np.eye(m)).max() < 1e-9
     # left vectors: L^dag A = Lambda L^dag
     assert np.linalg.norm(L.conj().T @ small["Ad"] - lam[:, None] * L.conj().T) < 1e-9 * np.linalg.norm(L)
+
+
+def test_lr_result_lies_in_its_search_space(small):
+    """Eq. 22 combines R_m and the Krylov vectors of x_minus only: the LR
+    approximation lies in span(R_m) + K_k(A, x_minus), and the orthogonal
+    projection of the exact result on that space is at least as close."""
+    m, k = 8, 25
+    R, L, lam = small["R"][:, :m], small["L"][:, :m], small["lam"][:m]
+    y = krylov.sign_lr(small["A"], small["b"], k, R, lam, L)
+    Q = krylov.lr_search_space(small["A"], small["b"], k, R, L)
+    assert Q.shape == (small["N"], m + k)
+    assert rel(krylov.best_approximation(Q, y), y) < 1e-12
+    yb = krylov.best_approximation(Q, small["ystar"])
+    assert rel(yb, small["ystar"]) <= rel(y, small["ystar"]) * (1 + 1e-12)
+    # the space is not the whole space: the projection changes the exact result
+    assert rel(yb, small["ystar"]) > 1e-8
