@@ -1,0 +1,88 @@
+"""Host logic of the (k, m) predictor on the CPU: labels, the cost model, the
+handling of an eigensolver that does not converge for one m, and the choice
+of the cost-minimal (k, m), with a stand-in for the library calls."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_0710_0341_gb300 import predictor
+
+
+class _OvlError(RuntimeError):
+    def __init__(self, infos=None):
+        super().__init__("stand-in failure")
+        self.infos = infos
+
+
+class _FakeOvl:
+    """Deflation setup fails for m = 16; the adaptive depth falls with m."""
+    OVL_DEFL_SCHUR = 1
+    OvlError = _OvlError
+
+    def __init__(self, k_of_m, fail_solve=False):
+        self.k_of_m = k_of_m
+        self.fail_solve = fail_solve
+        self.destroyed = []
+        self.batches = []
+
+    def ovl_deflation_setup(self, h, mu, m_w, scheme, m, tol, max_restarts):
+        if m == 16:
+            raise _OvlError()
+        return ("defl", m)
+
+    def ovl_deflation_stats(self, d):
+        return (3, 1000)  # restarts, A^2 applications
+
+    def ovl_sign_apply(self, h, params, defl, b, y):
+        ms = [0 if d is None else d[1] for d in defl]
+        self.batches.append(ms)
+        infos = [dict(status=0, k_used=self.k_of_m[m], err_est=1e-10) for m in ms]
+        if self.fail_solve:
+            infos[-1] = dict(status=4, k_used=600, err_est=1e-3)
+            raise _OvlError(infos)
+        return infos
+
+    def ovl_destroy_deflation(self, d):
+        self.destroyed.append(d)
+
+
+def test_measure_costs_and_skips_a_failed_setup(monkeypatch):
+    fake = _FakeOvl({0: 200, 8: 150, 24: 100})
+    monkeypatch.setattr(predictor, "ovl", fake)
+    res = predictor.measure(None, 0.3, -1.0, np.zeros((2, 3)), sources=12)
+    assert fake.batches == [[0, 8, 24]]  # one batch over the m whose setup converged
+    by_m = {r["m"]: r for r in res}
+    assert [r["m"] for r in res] == [0, 8, 16, 24]
+    assert by_m[16]["ok"] is False and by_m[16]["cost"] == float("inf")
+    assert by_m[0]["cost"] == 200 * (200 / 2 + 0)
+    sp = predictor.setup_passes(1000, 24) / 12
+    assert by_m[24]["cost"] == pytest.approx(100 * (100 / 2 + 24) + sp)
+    assert sorted(fake.destroyed) == [("defl", 8), ("defl", 24)]
+
+
+def test_measure_keeps_the_solves_that_finished(monkeypatch):
+    fake = _FakeOvl({0: 200, 8: 150, 24: 100}, fail_solve=True)
+    monkeypatch.setattr(predictor, "ovl", fake)
+    res = {r["m"]: r for r in predictor.measure(None, 0.3, -1.0, np.zeros(1))}
+    assert res[0]["ok"] and res[8]["ok"] and not res[24]["ok"]
+
+
+def test_setup_cost_and_labels():
+    # basis of at least nev + 60 and 4 nev vectors, nev = m + max(8, m/2)
+    assert predictor.setup_passes(10, 8) == 10 * max(4 * 16, 16 + 60)
+    assert predictor.setup_passes(10, 40) == 10 * 4 * 60
+    rows = [dict(features=[0.0] * predictor.N_IN, label=[120, 8]),
+            dict(features=[1.0] * predictor.N_IN, label=None),
+            dict(features=[2.0] * predictor.N_IN, label=[300, 0])]
+    X, T = predictor.to_xy(rows)
+    assert X.shape == (2, predictor.N_IN) and X.dtype == np.float32
+    assert np.allclose(T, [[math.log(120), math.log(9)], [math.log(300), 0.0]])
+    assert [predictor.nearest_m(v) for v in (-3, 5, 13, 19.9, 100)] == [0, 8, 16, 16, 24]
+
+
+def test_random_configs_stay_in_the_training_ranges():
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        c = predictor.random_config(rng)
+        assert 0.2 <= c["eps"] <= 0.6 and 0.0 <= c["mu"] <= 0.6 and -1.5 <= c["m_w"] <= -0.8
