@@ -61,9 +61,11 @@ typedef struct ovl_deflation_s*  ovl_deflation;
 #define OVL_VEC_F64  0   /* complex128 */
 #define OVL_VEC_F32  1   /* complex64  */
 /* Link formats for the stencil-only entry points. */
-#define OVL_LINKS_F64  0
-#define OVL_LINKS_F32  1
-#define OVL_LINKS_R12  2
+#define OVL_LINKS_F64    0
+#define OVL_LINKS_F32    1
+#define OVL_LINKS_R12    2
+#define OVL_LINKS_F64DF  3  /* FP64 links and spinors, double-float arithmetic (hi + lo FP32,
+                             * about 2^-46 relative error per application) on the FP32 pipes */
 
 typedef struct {
     double mu;          /* chemical potential (Eq. 2) */
@@ -117,7 +119,8 @@ int ovl_set_links(ovl_lattice lat, const double* U);
 /* ---- the operator (Sec. 1, Eq. 2): y = H_w(mu) x = gamma_5 D_w(mu) x ---- */
 
 /* nrhs right-hand sides, canonical layout, stride 24*V doubles between them.
- * links: OVL_LINKS_* selects the stencil arithmetic (F64: FP64; F32/R12: FP32). */
+ * links: OVL_LINKS_* selects the stencil arithmetic (F64: FP64; F64DF: double-float on
+ * FP64 data; F32/R12: FP32). */
 int ovl_apply_Hw(ovl_lattice lat, double mu, double m_w, const double* in, double* out,
                  int nrhs, int links);
 
@@ -139,7 +142,7 @@ int ovl_apply_Hw_noalloc(ovl_lattice lat, double mu, double m_w, const double* i
 /* Stencil on packed spinors (the library's internal site order), for timing
  * the stencil alone. in/out: device pointers, nrhs vectors of 12*V complex in
  * format fmt (OVL_VEC_*); mu: nrhs chemical potentials (host array).
- * fmt F64 requires links F64; fmt F32 takes F32 or R12 links. */
+ * fmt F64 requires links F64 or F64DF; fmt F32 takes F32 or R12 links. */
 int ovl_apply_Hw_packed(ovl_lattice lat, const double* mu, double m_w, const void* in,
                         void* out, int nrhs, int fmt, int links);
 /* Canonical complex128 <-> packed format (device or host canonical side;

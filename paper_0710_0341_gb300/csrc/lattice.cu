@@ -301,7 +301,7 @@ static int dslash_packed(ovl_lattice lat, const double* mu_host, double m_w, con
     da.nrhs = nrhs;
     da.kappa = 1.0 / (8.0 + 2.0 * m_w);
     const double sb = fmt == OVL_VEC_F64 ? 16.0 : 8.0;
-    const double lb = links == OVL_LINKS_F64 ? 144.0 : links == OVL_LINKS_F32 ? 72.0 : 48.0;
+    const double lb = (links == OVL_LINKS_F64 || links == OVL_LINKS_F64DF) ? 144.0 : links == OVL_LINKS_F32 ? 72.0 : 48.0;
     ProfScope ps(lat, 0, nrhs * (double)lat->V * (24.0 * sb + 4.0 * lb), lat->stream);
     int rc = ovl_dslash_launch(lat, da, fmt, links, lat->stream);
     ps.end(lat->stream);
@@ -316,9 +316,9 @@ extern "C" int ovl_apply_Hw_packed(ovl_lattice lat, const double* mu, double m_w
     if (!lat->have_links) return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw_packed: links not set");
     if (int rc = check_fmt(lat, fmt)) return rc;
     if (int rc = check_mw(lat, m_w)) return rc;
-    if (links < OVL_LINKS_F64 || links > OVL_LINKS_R12) return ovl_fail(lat, OVL_EINVAL, "bad links format %d", links);
-    if ((fmt == OVL_VEC_F64) != (links == OVL_LINKS_F64))
-        return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw_packed: F64 vectors go with F64 links, F32 with F32/R12");
+    if (links < OVL_LINKS_F64 || links > OVL_LINKS_F64DF) return ovl_fail(lat, OVL_EINVAL, "bad links format %d", links);
+    if ((fmt == OVL_VEC_F64) != (links == OVL_LINKS_F64 || links == OVL_LINKS_F64DF))
+        return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw_packed: F64 vectors go with F64/F64DF links, F32 with F32/R12");
     if (!ovl_is_device_ptr(in) || !ovl_is_device_ptr(out))
         return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw_packed: in/out must be device memory");
     if (in == out) return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw_packed: in and out must differ");
@@ -332,8 +332,8 @@ extern "C" int ovl_apply_Hw(ovl_lattice lat, double mu, double m_w, const double
     if (!lat || !in || !out || nrhs < 1) return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw: bad argument");
     if (!lat->have_links) return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw: links not set");
     if (int rc = check_mw(lat, m_w)) return rc;
-    if (links < OVL_LINKS_F64 || links > OVL_LINKS_R12) return ovl_fail(lat, OVL_EINVAL, "bad links format %d", links);
-    int fmt = links == OVL_LINKS_F64 ? OVL_VEC_F64 : OVL_VEC_F32;
+    if (links < OVL_LINKS_F64 || links > OVL_LINKS_F64DF) return ovl_fail(lat, OVL_EINVAL, "bad links format %d", links);
+    int fmt = (links == OVL_LINKS_F64 || links == OVL_LINKS_F64DF) ? OVL_VEC_F64 : OVL_VEC_F32;
     size_t cb = lat->N * sizeof(double2) * nrhs;  // canonical bytes
     size_t pb = ovl_vec_bytes(lat, fmt) * nrhs;   // packed bytes
     size_t off_in = 0, off_pin = cb, off_pout = off_pin + pb, off_args = off_pout + pb;

@@ -53,12 +53,12 @@ extern "C" int ovl_apply_Hw_noalloc(ovl_lattice lat, double mu, double m_w, cons
     if (!lat->have_links) return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw_noalloc: links not set");
     if (!(m_w > -4.0 + 1e-12) || !(m_w < 1e6))
         return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw_noalloc: m_w=%g gives no finite kappa", m_w);
-    if (links < OVL_LINKS_F64 || links > OVL_LINKS_R12)
+    if (links < OVL_LINKS_F64 || links > OVL_LINKS_F64DF)
         return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw_noalloc: bad links format %d", links);
     if (!ovl_is_device_ptr(in) || !ovl_is_device_ptr(out))
         return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw_noalloc: in and out must be device memory");
     if (in == out) return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw_noalloc: in and out must differ");
-    const int fmt = links == OVL_LINKS_F64 ? OVL_VEC_F64 : OVL_VEC_F32;
+    const int fmt = (links == OVL_LINKS_F64 || links == OVL_LINKS_F64DF) ? OVL_VEC_F64 : OVL_VEC_F32;
     const size_t vb = ovl_vec_bytes(lat, fmt) * (size_t)nrhs;  // one packed block
     const size_t vba = (vb + 255) & ~(size_t)255;
     const size_t args = 3 * sizeof(double) * (size_t)nrhs;      // in/out pointers and mu
