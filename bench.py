@@ -387,10 +387,11 @@ def replica_throughput(ms_local, units_local, ws, device):
 
 def stencil_gbs(torch, ovl, synth):
     """Stencil-only launches on packed spinors at sizes above L2: 24^3x48 with
-    one right-hand side (three link formats) and 16^3x32 with 12 right-hand
-    sides in one launch. Algorithmic bytes per launch: spinors in and out per
+    one right-hand side (three link formats, and the FP64 data with double-float
+    arithmetic) and 16^3x32 with 12 right-hand sides in one launch. Algorithmic bytes per launch: spinors in and out per
     right-hand side plus the four links of each site once."""
     cases = (((24, 24, 24, 48), 1, (("fp32_r12", 1, 2, 8, 48), ("fp32_18", 1, 1, 8, 72), ("fp64", 0, 0, 16, 144))),
+             ((24, 24, 24, 48), 1, (("fp64_double_float", 0, 3, 16, 144),)),
              ((16, 16, 16, 32), 12, (("fp32_r12_16x3x32_12rhs", 1, 2, 8, 48),)))
     res = {}
     for dims, nrhs, fmts in cases:

@@ -154,14 +154,16 @@ def test_stencil_cases_count_spinors_per_rhs_and_links_once():
     assert not lib.lat  # every lattice destroyed
     V24, V16 = 24 ** 3 * 48, 16 ** 3 * 32
     expect = {"fp32_r12": (V24, 1, 2 * 12 * 8 + 4 * 48), "fp32_18": (V24, 1, 2 * 12 * 8 + 4 * 72),
-              "fp64": (V24, 1, 2 * 12 * 16 + 4 * 144), "fp32_r12_16x3x32_12rhs": (V16, 12, 12 * 2 * 12 * 8 + 4 * 48)}
+              "fp64": (V24, 1, 2 * 12 * 16 + 4 * 144), "fp64_double_float": (V24, 1, 2 * 12 * 16 + 4 * 144),
+              "fp32_r12_16x3x32_12rhs": (V16, 12, 12 * 2 * 12 * 8 + 4 * 48)}
     for name, (V, nrhs, bps) in expect.items():
         r = res[name]
         assert r["rhs"] == nrhs and r["bytes_per_site"] == bps
         assert abs(r["us_per_launch"] - 10.0) < 1e-9
         assert abs(r["GB_per_s"] - V * bps / 10e-6 / 1e9) < 1e-6 * r["GB_per_s"]
     # 3 warm-up and 20 timed launches per case, the 12-rhs case in one launch each
-    assert len(lib.calls) == 4 * 23 and lib.calls[-1] == ((16, 16, 16, 32), 12, 1, 2)
+    assert len(lib.calls) == 5 * 23 and lib.calls[-1] == ((16, 16, 16, 32), 12, 1, 2)
+    assert ((24, 24, 24, 48), 1, 0, 3) in lib.calls  # FP64 data, double-float links format
 
 
 def test_amortised_throughput_includes_the_setup():
