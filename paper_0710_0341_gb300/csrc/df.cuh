@@ -9,39 +9,57 @@
 // fused operations, which would break exactness.
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
+
+// Every function here is __host__ __device__ (a host build checks the
+// arithmetic on the CPU); on the device the single-precision steps use the
+// *_rn intrinsics, on the host plain IEEE operations (built without FP
+// contraction) with the same results.
+#define DF_HD __host__ __device__ __forceinline__
+#ifdef __CUDA_ARCH__
+#define DF_ADD(a, b) __fadd_rn(a, b)
+#define DF_SUB(a, b) __fsub_rn(a, b)
+#define DF_MUL(a, b) __fmul_rn(a, b)
+#define DF_FMA(a, b, c) __fmaf_rn(a, b, c)
+#else
+#define DF_ADD(a, b) ((float)(a) + (float)(b))
+#define DF_SUB(a, b) ((float)(a) - (float)(b))
+#define DF_MUL(a, b) ((float)(a) * (float)(b))
+#define DF_FMA(a, b, c) fmaf(a, b, c)
+#endif
 
 struct dfc {  // complex df: (re_hi, im_hi) + (re_lo, im_lo)
     float2 hi, lo;
 };
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+DF_HD void two_sum(float a, float b, float& s, float& e) {
+    s = DF_ADD(a, b);
+    float bb = DF_SUB(s, a);
+    e = DF_ADD(DF_SUB(a, DF_SUB(s, bb)), DF_SUB(b, bb));
 }
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    e = __fsub_rn(b, __fsub_rn(s, a));
+DF_HD void fast_two_sum(float a, float b, float& s, float& e) {
+    s = DF_ADD(a, b);
+    e = DF_SUB(b, DF_SUB(s, a));
 }
-__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-    p = __fmul_rn(a, b);
-    e = __fmaf_rn(a, b, -p);
+DF_HD void two_prod(float a, float b, float& p, float& e) {
+    p = DF_MUL(a, b);
+    e = DF_FMA(a, b, -p);
 }
 
 // split an FP64 value into hi + lo FP32 (exact to 48 bits)
-__host__ __device__ __forceinline__ float2 split_d(double x) {
+DF_HD float2 split_d(double x) {
     float h = (float)x;
     float l = (float)(x - (double)h);
     return make_float2(h, l);
 }
-__device__ __forceinline__ dfc dfc_from(double2 z) {
+DF_HD dfc dfc_from(double2 z) {
     float2 a = split_d(z.x), b = split_d(z.y);
     dfc r;
     r.hi = make_float2(a.x, b.x);
     r.lo = make_float2(a.y, b.y);
     return r;
 }
-__device__ __forceinline__ double2 dfc_to(const dfc& z) {
+DF_HD double2 dfc_to(const dfc& z) {
     return make_double2((double)z.hi.x + (double)z.lo.x, (double)z.hi.y + (double)z.lo.y);
 }
 
@@ -53,22 +71,22 @@ struct dfacc {
     float2 s;  // hi sum
     float2 t;  // low-order terms
 };
-__device__ __forceinline__ void dfacc_zero(dfacc& a) {
+DF_HD void dfacc_zero(dfacc& a) {
     a.s = make_float2(0.f, 0.f);
     a.t = make_float2(0.f, 0.f);
 }
 // a += q * g (complex), q = qh + ql, g = gh + gl
-__device__ __forceinline__ void dfacc_mac(dfacc& a, float2 qh, float2 ql, float2 gh, float2 gl) {
+DF_HD void dfacc_mac(dfacc& a, float2 qh, float2 ql, float2 gh, float2 gl) {
     float p, e, s, err;
     // real part: qh.x*gh.x - qh.y*gh.y
     two_prod(qh.x, gh.x, p, e);
     two_sum(a.s.x, p, s, err);
     a.s.x = s;
-    a.t.x = __fadd_rn(a.t.x, __fadd_rn(err, e));
+    a.t.x = DF_ADD(a.t.x, DF_ADD(err, e));
     two_prod(-qh.y, gh.y, p, e);
     two_sum(a.s.x, p, s, err);
     a.s.x = s;
-    a.t.x = __fadd_rn(a.t.x, __fadd_rn(err, e));
+    a.t.x = DF_ADD(a.t.x, DF_ADD(err, e));
     a.t.x = fmaf(qh.x, gl.x, a.t.x);
     a.t.x = fmaf(-qh.y, gl.y, a.t.x);
     a.t.x = fmaf(ql.x, gh.x, a.t.x);
@@ -77,48 +95,48 @@ __device__ __forceinline__ void dfacc_mac(dfacc& a, float2 qh, float2 ql, float2
     two_prod(qh.x, gh.y, p, e);
     two_sum(a.s.y, p, s, err);
     a.s.y = s;
-    a.t.y = __fadd_rn(a.t.y, __fadd_rn(err, e));
+    a.t.y = DF_ADD(a.t.y, DF_ADD(err, e));
     two_prod(qh.y, gh.x, p, e);
     two_sum(a.s.y, p, s, err);
     a.s.y = s;
-    a.t.y = __fadd_rn(a.t.y, __fadd_rn(err, e));
+    a.t.y = DF_ADD(a.t.y, DF_ADD(err, e));
     a.t.y = fmaf(qh.x, gl.y, a.t.y);
     a.t.y = fmaf(qh.y, gl.x, a.t.y);
     a.t.y = fmaf(ql.x, gh.y, a.t.y);
     a.t.y = fmaf(ql.y, gh.x, a.t.y);
 }
 // merge b into a (both accumulators)
-__device__ __forceinline__ void dfacc_add(dfacc& a, const dfacc& b) {
+DF_HD void dfacc_add(dfacc& a, const dfacc& b) {
     float s, err;
     two_sum(a.s.x, b.s.x, s, err);
     a.s.x = s;
-    a.t.x = __fadd_rn(a.t.x, __fadd_rn(err, b.t.x));
+    a.t.x = DF_ADD(a.t.x, DF_ADD(err, b.t.x));
     two_sum(a.s.y, b.s.y, s, err);
     a.s.y = s;
-    a.t.y = __fadd_rn(a.t.y, __fadd_rn(err, b.t.y));
+    a.t.y = DF_ADD(a.t.y, DF_ADD(err, b.t.y));
 }
-__device__ __forceinline__ double2 dfacc_value(const dfacc& a) {
+DF_HD double2 dfacc_value(const dfacc& a) {
     return make_double2((double)a.s.x + (double)a.t.x, (double)a.s.y + (double)a.t.y);
 }
 
 // ---- complex df values (Newton sign): hi + lo, each a complex FP32 -------
-__device__ __forceinline__ dfc dfc_make(float2 hi, float2 lo) {
+DF_HD dfc dfc_make(float2 hi, float2 lo) {
     dfc r;
     r.hi = hi;
     r.lo = lo;
     return r;
 }
-__device__ __forceinline__ float4 dfc_pack(const dfc& a) { return make_float4(a.hi.x, a.hi.y, a.lo.x, a.lo.y); }
-__device__ __forceinline__ dfc dfc_unpack(float4 v) { return dfc_make(make_float2(v.x, v.y), make_float2(v.z, v.w)); }
+DF_HD float4 dfc_pack(const dfc& a) { return make_float4(a.hi.x, a.hi.y, a.lo.x, a.lo.y); }
+DF_HD dfc dfc_unpack(float4 v) { return dfc_make(make_float2(v.x, v.y), make_float2(v.z, v.w)); }
 // renormalise a real df pair (s, t) so that |t| <= ulp(s)/2
-__device__ __forceinline__ void df_norm(float& s, float& t) {
+DF_HD void df_norm(float& s, float& t) {
     float a, b;
     fast_two_sum(s, t, a, b);
     s = a;
     t = b;
 }
 // c - a * b  (all complex df), error about 2^-46 relative to |a||b| + |c|
-__device__ __forceinline__ dfc dfc_fms(const dfc& c, const dfc& a, const dfc& b) {
+DF_HD dfc dfc_fms(const dfc& c, const dfc& a, const dfc& b) {
     float p, e, s, err;
     dfc r;
     // real: c.re - (a.re b.re - a.im b.im)
@@ -126,11 +144,11 @@ __device__ __forceinline__ dfc dfc_fms(const dfc& c, const dfc& a, const dfc& b)
     two_prod(a.hi.x, b.hi.x, p, e);
     two_sum(sr, -p, s, err);
     sr = s;
-    tr = __fadd_rn(tr, __fsub_rn(err, e));
+    tr = DF_ADD(tr, DF_SUB(err, e));
     two_prod(a.hi.y, b.hi.y, p, e);
     two_sum(sr, p, s, err);
     sr = s;
-    tr = __fadd_rn(tr, __fadd_rn(err, e));
+    tr = DF_ADD(tr, DF_ADD(err, e));
     tr = fmaf(-a.hi.x, b.lo.x, tr);
     tr = fmaf(-a.lo.x, b.hi.x, tr);
     tr = fmaf(a.hi.y, b.lo.y, tr);
@@ -141,11 +159,11 @@ __device__ __forceinline__ dfc dfc_fms(const dfc& c, const dfc& a, const dfc& b)
     two_prod(a.hi.x, b.hi.y, p, e);
     two_sum(si, -p, s, err);
     si = s;
-    ti = __fadd_rn(ti, __fsub_rn(err, e));
+    ti = DF_ADD(ti, DF_SUB(err, e));
     two_prod(a.hi.y, b.hi.x, p, e);
     two_sum(si, -p, s, err);
     si = s;
-    ti = __fadd_rn(ti, __fsub_rn(err, e));
+    ti = DF_ADD(ti, DF_SUB(err, e));
     ti = fmaf(-a.hi.x, b.lo.y, ti);
     ti = fmaf(-a.lo.x, b.hi.y, ti);
     ti = fmaf(-a.hi.y, b.lo.x, ti);
@@ -155,10 +173,10 @@ __device__ __forceinline__ dfc dfc_fms(const dfc& c, const dfc& a, const dfc& b)
     r.lo = make_float2(tr, ti);
     return r;
 }
-__device__ __forceinline__ dfc dfc_zero() { return dfc_make(make_float2(0.f, 0.f), make_float2(0.f, 0.f)); }
-__device__ __forceinline__ dfc dfc_mul(const dfc& a, const dfc& b) { return dfc_fms(dfc_zero(), dfc_make(make_float2(-a.hi.x, -a.hi.y), make_float2(-a.lo.x, -a.lo.y)), b); }
+DF_HD dfc dfc_zero() { return dfc_make(make_float2(0.f, 0.f), make_float2(0.f, 0.f)); }
+DF_HD dfc dfc_mul(const dfc& a, const dfc& b) { return dfc_fms(dfc_zero(), dfc_make(make_float2(-a.hi.x, -a.hi.y), make_float2(-a.lo.x, -a.lo.y)), b); }
 // s * a + t * b for real FP64 scalars s, t (via FP64 on the two parts: used once per element per iteration)
-__device__ __forceinline__ dfc dfc_axpby(double s, const dfc& a, double t, const dfc& b) {
+DF_HD dfc dfc_axpby(double s, const dfc& a, double t, const dfc& b) {
     double2 x = dfc_to(a), y = dfc_to(b);
     return dfc_from(make_double2(s * x.x + t * y.x, s * x.y + t * y.y));
 }
