@@ -142,3 +142,37 @@ def test_double_float_conversion_and_operations(lib):
     o2 = np.zeros(15)
     lib.host_dd_ops(_ptr(nan_inf), _ptr(np.ones(3)), _ptr(np.ones(3)), _ptr(np.ones(3)), _ptr(o2), 3)
     assert np.isnan(o2[0]) and o2[5] == np.inf and o2[10] == -np.inf
+
+
+class _HostOperator:
+    """H_w(mu) applied by a host build of one stencil instantiation (for the
+    oracle's Arnoldi, which takes anything with A @ v)."""
+
+    def __init__(self, lib, U, mu, m_w, mode):
+        self.lib, self.U, self.mu, self.m_w, self.mode = lib, U, mu, m_w, mode
+        self.shape = U.shape[:4] + (4, 3)
+
+    def __matmul__(self, v):
+        return _apply(self.lib, self.U, np.asarray(v).reshape(self.shape), self.mu, self.m_w, 0, self.mode).ravel()
+
+
+def test_sign_function_with_double_float_matvecs(lib):
+    """What the FP64 mode's result would lose with the double-float stencil: the
+    oracle's deflated and undeflated approximations of sgn(H_w) b driven by the
+    host build of that stencil differ from those with the exact operator by far
+    less than the 1e-10 parity bar."""
+    from oracle import eigen, krylov
+
+    dims, mu, m_w = (2, 2, 2, 4), 0.3, -1.0
+    U = synth.random_su3_field(dims, 0.5, 0)
+    A = dirac.hermitian_wilson(U, mu, m_w)
+    Add = _HostOperator(lib, U, mu, m_w, 1)
+    b = synth.gaussian_source(dims, 1).ravel()
+    lam, R, L = eigen.critical_dense(A.toarray(), 16)
+    S, T = eigen.schur_from_right(A, R[:, :12])
+    for f in (lambda Op: krylov.sign_arnoldi(Op, b, 80),
+              lambda Op: krylov.sign_lr(Op, b, 60, R, lam, L),
+              lambda Op: krylov.sign_schur_block(Op, b, 60, S, T)):
+        y, ydd = f(A), f(Add)
+        d = np.linalg.norm(ydd - y) / np.linalg.norm(y)
+        assert d < 1e-12, d
