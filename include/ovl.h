@@ -51,6 +51,8 @@ typedef struct ovl_deflation_s*  ovl_deflation;
                                   FP64 Newton, projections and recombination */
 #define OVL_PREC_MIXED      1  /* FP32 stencil (18-real links), FP32 basis, FP64 coefficients */
 #define OVL_PREC_MIXED_R12  2  /* as OVL_PREC_MIXED with 12-real (two-row) links */
+#define OVL_PREC_FP64_DFSTENCIL 3  /* as OVL_PREC_FP64 with the stencil's arithmetic in double-float
+                                      (OVL_LINKS_F64DF) on the FP32 pipes */
 
 /* Deflation scheme (Sec. 3 Schur, Sec. 4 LR). */
 #define OVL_DEFL_NONE   0

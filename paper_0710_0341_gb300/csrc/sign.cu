@@ -235,9 +235,9 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     const size_t N = lat->N;
     const int prec = params[0].prec;
     const double m_w = params[0].m_w;
-    if (prec < OVL_PREC_FP64 || prec > OVL_PREC_MIXED_R12)
+    if (prec < OVL_PREC_FP64 || prec > OVL_PREC_FP64_DFSTENCIL)
         return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: precision %d unknown", prec);
-    const bool df = prec == OVL_PREC_FP64;
+    const bool df = prec == OVL_PREC_FP64 || prec == OVL_PREC_FP64_DFSTENCIL;  // hi + lo basis
     std::vector<SolvePlan> P(nsolve);
     int kmax = 0, ldmax = 0, mdef_max = 0;
     for (int i = 0; i < nsolve; i++) {
@@ -563,8 +563,12 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     da.stride = (int)(sizeof(SolveDev) / sizeof(int));
     da.nrhs = nsolve;
     da.kappa = 1.0 / (8.0 + 2.0 * m_w);
-    const int links = prec == OVL_PREC_FP64 ? OVL_LINKS_F64 : prec == OVL_PREC_MIXED ? OVL_LINKS_F32 : OVL_LINKS_R12;
-    const double site_bytes = 2.0 * 12 * 16 + 4.0 * (links == OVL_LINKS_F64 ? 144 : links == OVL_LINKS_F32 ? 72 : 48);
+    const int links = prec == OVL_PREC_FP64             ? OVL_LINKS_F64
+                      : prec == OVL_PREC_FP64_DFSTENCIL ? OVL_LINKS_F64DF
+                      : prec == OVL_PREC_MIXED          ? OVL_LINKS_F32
+                                                        : OVL_LINKS_R12;
+    const double site_bytes =
+        2.0 * 12 * 16 + 4.0 * ((links == OVL_LINKS_F64 || links == OVL_LINKS_F64DF) ? 144 : links == OVL_LINKS_F32 ? 72 : 48);
     const double qbytes = df ? 16.0 : 8.0;
     bool any_adapt = false;
     for (int i = 0; i < nsolve; i++) any_adapt = any_adapt || P[i].adapt > 0;

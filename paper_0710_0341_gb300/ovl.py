@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(_HERE, "libovl.so")
 
 OVL_OK, OVL_EINVAL, OVL_ENOMEM, OVL_ECUDA, OVL_ENOCONV, OVL_ETIMEOUT, OVL_ENOTSUP = range(7)
-OVL_PREC_FP64, OVL_PREC_MIXED, OVL_PREC_MIXED_R12 = 0, 1, 2
+OVL_PREC_FP64, OVL_PREC_MIXED, OVL_PREC_MIXED_R12, OVL_PREC_FP64_DFSTENCIL = 0, 1, 2, 3
 OVL_DEFL_NONE, OVL_DEFL_SCHUR, OVL_DEFL_LR = 0, 1, 2
 OVL_VEC_F64, OVL_VEC_F32 = 0, 1
 OVL_LINKS_F64, OVL_LINKS_F32, OVL_LINKS_R12, OVL_LINKS_F64DF = 0, 1, 2, 3

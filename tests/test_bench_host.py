@@ -58,7 +58,7 @@ class _Torch:
 
 
 class _Lib:
-    OVL_PREC_FP64, OVL_PREC_MIXED, OVL_PREC_MIXED_R12 = 0, 1, 2
+    OVL_PREC_FP64, OVL_PREC_MIXED, OVL_PREC_MIXED_R12, OVL_PREC_FP64_DFSTENCIL = 0, 1, 2, 3
 
     def __init__(self):
         self.calls = []
@@ -69,19 +69,20 @@ class _Lib:
 
 
 def test_mixed_modes_times_both_modes_on_the_batch(monkeypatch):
-    errs = {1: [5e-8] * 8, 2: [7e-8] * 7 + [2e-7]}
+    errs = {1: [5e-8] * 8, 2: [7e-8] * 7 + [2e-7], 3: [2e-9] * 8}
     lib = _Lib()
     monkeypatch.setattr(bench, "reference_sketch", lambda: {"0.0": {}})
     monkeypatch.setattr(bench, "accuracy", lambda y, sk: errs[lib.calls[-1][0]])
     bd = _Tensor(np.ones((8, 4), complex))
     out = bench.mixed_modes(_Torch, lib, None, [None] * 8, bd, 3)
     # one warm-up and three timed calls per mode, each over the 8-solve batch in one precision
-    assert [c[0] for c in lib.calls] == [1] * 4 + [2] * 4
+    assert [c[0] for c in lib.calls] == [1] * 4 + [2] * 4 + [3] * 4
     assert all(len(set(c)) == 1 and len(c) == 8 for c in lib.calls)
     a, b = out["fp32_basis_fp32_links"], out["fp32_basis_r12_links"]
     assert abs(a["ms_per_step"] - 50.0 / 3) < 1e-9
     assert abs(a["solves_per_s"] - 8 / (50.0 / 3 / 1e3)) < 1e-6
     assert a["meets_1e-8"] is False and b["rel_err_est_per_solve"][-1] == 2e-7
+    assert out["fp64_basis_double_float_stencil"]["meets_1e-8"] is True
 
 
 class _Buf:

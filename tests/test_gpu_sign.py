@@ -384,3 +384,37 @@ def test_uneven_batch_full_size_12x4():
         assert 0.5 < np.linalg.norm(yb[3]) / np.linalg.norm(b) < 1.5
     finally:
         ovl.ovl_destroy_lattice(h)
+
+
+@pytest.mark.parametrize("dims", [DIMS, (3, 4, 2, 5)])
+def test_fp64_mode_with_double_float_stencil(dims):
+    """OVL_PREC_FP64_DFSTENCIL (the FP64 mode with the stencil's arithmetic in
+    double-float on the FP32 pipes) against the oracle's same algorithm at the
+    FP64 mode's 1e-10 bar, for Schur, LR and no deflation in one batch, and
+    within 1e-12 of the FP64 mode itself."""
+    need_gpu()
+    mu, m_w = 0.3, -1.0
+    U, A = _setup(dims, 0.5, mu, m_w)
+    S, T, lam, R, L = _schur(A, dims, 12)
+    b = synth.gaussian_source(dims, 1)
+    h = lattice(dims, U)
+    try:
+        ds = _defl_schur(h, mu, m_w, S, T, dims)
+        dl = _defl_lr(h, mu, m_w, lam, R, L, dims)
+        k = 60
+        bb = np.stack([b, b, b])
+        ys = {}
+        for prec in (ovl.OVL_PREC_FP64, ovl.OVL_PREC_FP64_DFSTENCIL):
+            y = np.zeros_like(bb)
+            infos = ovl.ovl_sign_apply(h, [dict(mu=mu, m_w=m_w, k=k, prec=prec)] * 3, [ds, dl, None], bb, y)
+            assert all(i["status"] == 0 for i in infos)
+            ys[prec] = y
+        refs = [krylov.sign_schur(A, b.ravel(), k, S, T), krylov.sign_lr(A, b.ravel(), k, R, lam, L),
+                krylov.sign_arnoldi(A, b.ravel(), k)]
+        for i in range(3):
+            assert rel(ys[ovl.OVL_PREC_FP64_DFSTENCIL][i], refs[i]) < 1e-10, (i, rel(ys[3][i], refs[i]))
+            assert rel(ys[ovl.OVL_PREC_FP64_DFSTENCIL][i], ys[ovl.OVL_PREC_FP64][i]) < 1e-12
+        for d in (ds, dl):
+            ovl.ovl_destroy_deflation(d)
+    finally:
+        ovl.ovl_destroy_lattice(h)
