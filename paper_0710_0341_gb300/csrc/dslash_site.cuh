@@ -209,11 +209,16 @@ OVL_HD void project(const C<T> (&psi)[12], C<T> (&h)[6]) {
     }
 }
 
+// w multiplies the time hops only (NU == 3); a spatial hop's weight is 1
 template <typename T, int NU, bool FWD>
 OVL_HD void expand_add(const C<T> (&g)[6], T w, C<T> (&acc)[12]) {
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        C<T> g0 = w * g[c], g1 = w * g[3 + c];
+        C<T> g0 = g[c], g1 = g[3 + c];
+        if constexpr (NU == 3) {
+            g0 = w * g0;
+            g1 = w * g1;
+        }
         acc[c] = acc[c] + g0;
         acc[3 + c] = acc[3 + c] + g1;
         C<T> r2, r3;
