@@ -11,9 +11,21 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: takes more than a few seconds on the CPU")
+    config.addinivalue_line("markers", "late(rank=1): run after every other test (see pytest_collection_modifyitems)")
     spec = os.environ.get("ORACLE_MUTANT")
     if spec:
         _plant_oracle_mutant(spec)
+
+
+def pytest_collection_modifyitems(config, items):
+    """Tests marked late run after all the others, ordered by the marker's
+    rank (late(2) after late) and otherwise as collected: under -x a failure
+    there leaves every other test already run."""
+    def rank(it):
+        m = it.get_closest_marker("late")
+        return 0 if m is None else (m.args[0] if m.args else 1)
+
+    items.sort(key=rank)
 
 
 def _plant_oracle_mutant(spec):

@@ -82,6 +82,7 @@ def test_error_vs_depth_lr_deflation_4x4():
         ovl.ovl_destroy_lattice(h)
 
 
+@pytest.mark.late(2)
 def test_error_vs_depth_lr_deflation_6x4_matches_the_oracle_table():
     """The 6^4 leg of the study (m up to 124 = 0.008 N): the CUDA path computes
     every (m, k) point of the oracle's stored table in one batched call, with

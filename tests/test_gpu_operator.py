@@ -135,6 +135,7 @@ def test_apply_hw_full_size_sampled(dims, eps, m_w):
         ovl.ovl_destroy_lattice(h)
 
 
+@pytest.mark.late
 @pytest.mark.parametrize("dims,apbc", [((4, 4, 4, 4), 0), ((3, 4, 2, 5), 1)])
 def test_apply_hw_double_float_arithmetic(dims, apbc):
     """OVL_LINKS_F64DF: the FP64 data through the double-float instantiation of

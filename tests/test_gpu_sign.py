@@ -386,6 +386,7 @@ def test_uneven_batch_full_size_12x4():
         ovl.ovl_destroy_lattice(h)
 
 
+@pytest.mark.late
 @pytest.mark.parametrize("dims", [DIMS, (3, 4, 2, 5)])
 def test_fp64_mode_with_double_float_stencil(dims):
     """OVL_PREC_FP64_DFSTENCIL (the FP64 mode with the stencil's arithmetic in
