@@ -24,6 +24,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include "df.cuh"
 #include "dslash_site.cuh"
 
 namespace ovl_stencil {
@@ -146,5 +147,36 @@ OVL_HD dd ffma(dd a, dd b, dd c) {
     dd_fast_two_sum(s, t, s, t);
     return dd(s, t);
 }
+
+// The link multiplication in double-float: each output is one accumulation of
+// three complex products (dfacc_mac of df.cuh: exact hi products, two_sum of
+// the hi parts, low-order terms in FP32), renormalised once at the end.
+template <>
+struct LinkMul<dd> {
+    template <bool FWD>
+    static OVL_HD void run(const C<dd> (&u)[9], const C<dd> (&h)[6], C<dd> (&g)[6]) {
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+#pragma unroll
+            for (int ai = 0; ai < 3; ai++) {
+                dfacc acc;
+                dfacc_zero(acc);
+#pragma unroll
+                for (int b = 0; b < 3; b++) {
+                    const C<dd> w = FWD ? u[3 * ai + b] : u[3 * b + ai];
+                    const C<dd> x = h[3 * s + b];
+                    // U h, or conj(U) h for U^dag h
+                    const float wih = FWD ? w.i.hi : -w.i.hi, wil = FWD ? w.i.lo : -w.i.lo;
+                    dfacc_mac(acc, make_float2(w.r.hi, wih), make_float2(w.r.lo, wil), make_float2(x.r.hi, x.i.hi),
+                              make_float2(x.r.lo, x.i.lo));
+                }
+                float rs, rt, is, it;
+                dd_two_sum(acc.s.x, acc.t.x, rs, rt);
+                dd_two_sum(acc.s.y, acc.t.y, is, it);
+                g[3 * s + ai] = C<dd>{dd(rs, rt), dd(is, it)};
+            }
+        }
+    }
+};
 
 }  // namespace ovl_stencil

@@ -240,6 +240,30 @@ OVL_HD void expand_add(const C<T> (&g)[6], T w, C<T> (&acc)[12]) {
     }
 }
 
+// g = U h (forward hop) or U^dag h (backward hop) for both spins of the half
+// spinor; dd.cuh specialises it for the double-float type
+template <typename T>
+struct LinkMul {
+    template <bool FWD>
+    static OVL_HD void run(const C<T> (&u)[9], const C<T> (&h)[6], C<T> (&g)[6]) {
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+#pragma unroll
+            for (int ai = 0; ai < 3; ai++) {
+                C<T> z = mk<T>(0, 0);
+#pragma unroll
+                for (int b = 0; b < 3; b++) {
+                    if constexpr (FWD)
+                        z = cfma(u[3 * ai + b], h[3 * s + b], z);  // U h
+                    else
+                        z = cjfma(u[3 * b + ai], h[3 * s + b], z);  // U^dag h
+                }
+                g[3 * s + ai] = z;
+            }
+        }
+    }
+};
+
 template <typename T, typename VT, int LINKS, int NU, bool FWD>
 OVL_HD void hop(const KArgs& a, const VT* __restrict__ in, size_t site, size_t nb, T w, C<T> (&acc)[12]) {
     C<T> psi[12];
@@ -249,21 +273,7 @@ OVL_HD void hop(const KArgs& a, const VT* __restrict__ in, size_t site, size_t n
     C<T> u[9];
     load_link<T, LINKS>(a, NU, FWD ? site : nb, u);
     C<T> g[6];
-#pragma unroll
-    for (int s = 0; s < 2; s++) {
-#pragma unroll
-        for (int ai = 0; ai < 3; ai++) {
-            C<T> z = mk<T>(0, 0);
-#pragma unroll
-            for (int b = 0; b < 3; b++) {
-                if constexpr (FWD)
-                    z = cfma(u[3 * ai + b], h[3 * s + b], z);  // U h
-                else
-                    z = cjfma(u[3 * b + ai], h[3 * s + b], z);  // U^dag h
-            }
-            g[3 * s + ai] = z;
-        }
-    }
+    LinkMul<T>::template run<FWD>(u, h, g);
     expand_add<T, NU, FWD>(g, w, acc);
 }
 

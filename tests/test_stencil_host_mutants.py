@@ -1,6 +1,6 @@
 """Planted mistakes in the stencil's site arithmetic are caught by the host check.
 
-Each case copies the kernel headers (dslash_site.cuh, dd.cuh, ovl.h) and the
+Each case copies the kernel headers (dslash_site.cuh, dd.cuh, df.cuh, ovl.h) and the
 host harness into a scratch tree, plants one slip in the copy, builds the
 harness against it and runs the comparison of tests/test_stencil_host.py for
 the instantiation it touches: the planted copy must miss the oracle by far
@@ -42,6 +42,9 @@ CASES = [
      "    float s, t;\n    dd_fast_two_sum(p, e, s, t);", 1, 2e-14),
     ("double-float conversion without the low part", "dd.cuh", "                lo = sgn ? -l : l;",
      "                lo = 0.f;", 1, 2e-14),
+    ("double-float U^dag without the conjugate", "dd.cuh",
+     "const float wih = FWD ? w.i.hi : -w.i.hi, wil = FWD ? w.i.lo : -w.i.lo;",
+     "const float wih = w.i.hi, wil = w.i.lo;", 1, 2e-14),
 ]
 
 
@@ -51,7 +54,7 @@ def _build(case, tmp):
     os.makedirs(os.path.join(d, "paper_0710_0341_gb300", "csrc"))
     os.makedirs(os.path.join(d, "include"))
     os.makedirs(os.path.join(d, "tests", "hostcheck"))
-    for h in ("dslash_site.cuh", "dd.cuh"):
+    for h in ("dslash_site.cuh", "dd.cuh", "df.cuh"):
         src = open(os.path.join(CSRC, h)).read()
         if h == header:
             assert src.count(old) == 1, (name, src.count(old))
