@@ -21,11 +21,13 @@
 #define DF_SUB(a, b) __fsub_rn(a, b)
 #define DF_MUL(a, b) __fmul_rn(a, b)
 #define DF_FMA(a, b, c) __fmaf_rn(a, b, c)
+#define DF_DIV(a, b) __fdiv_rn(a, b)
 #else
 #define DF_ADD(a, b) ((float)(a) + (float)(b))
 #define DF_SUB(a, b) ((float)(a) - (float)(b))
 #define DF_MUL(a, b) ((float)(a) * (float)(b))
 #define DF_FMA(a, b, c) fmaf(a, b, c)
+#define DF_DIV(a, b) ((float)(a) / (float)(b))
 #endif
 
 struct dfc {  // complex df: (re_hi, im_hi) + (re_lo, im_lo)
@@ -179,4 +181,26 @@ DF_HD dfc dfc_mul(const dfc& a, const dfc& b) { return dfc_fms(dfc_zero(), dfc_m
 DF_HD dfc dfc_axpby(double s, const dfc& a, double t, const dfc& b) {
     double2 x = dfc_to(a), y = dfc_to(b);
     return dfc_from(make_double2(s * x.x + t * y.x, s * x.y + t * y.y));
+}
+
+// 1 / z for a complex df value: conj(z) * (1 / |z|^2), the real reciprocal
+// refined by one Newton step in df (error about 2^-46 relative)
+DF_HD dfc dfc_inv(const dfc& z) {
+    float p1, e1, p2, e2, s, e;
+    two_prod(z.hi.x, z.hi.x, p1, e1);
+    two_prod(z.hi.y, z.hi.y, p2, e2);
+    two_sum(p1, p2, s, e);
+    float t = DF_ADD(DF_ADD(e, e1), e2);
+    t = fmaf(2.f * z.hi.x, z.lo.x, t);
+    t = fmaf(2.f * z.hi.y, z.lo.y, t);
+    df_norm(s, t);  // |z|^2 = s + t
+    const float r0 = DF_DIV(1.f, s);
+    float pr, pe;
+    two_prod(s, r0, pr, pe);
+    // residual 1 - (s + t) r0; 1 - pr is exact (pr is within an ulp of 1)
+    const float res = DF_SUB(DF_SUB(DF_SUB(1.f, pr), pe), DF_MUL(t, r0));
+    float rh, rl;
+    fast_two_sum(r0, DF_MUL(r0, res), rh, rl);
+    const dfc zc = dfc_make(make_float2(z.hi.x, -z.hi.y), make_float2(z.lo.x, -z.lo.y));
+    return dfc_mul(zc, dfc_make(make_float2(rh, 0.f), make_float2(rl, 0.f)));
 }

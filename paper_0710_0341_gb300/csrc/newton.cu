@@ -627,28 +627,6 @@ namespace cg = cooperative_groups;
 constexpr int NTC = 512;
 constexpr int GPF = 4;  // prefetched L2-row elements per thread and pivot
 
-// 1 / z for a complex df value: conj(z) * (1 / |z|^2), the real reciprocal
-// refined by one Newton step in df (error about 2^-46 relative)
-__device__ __forceinline__ dfc dfc_inv(const dfc& z) {
-    float p1, e1, p2, e2, s, e;
-    two_prod(z.hi.x, z.hi.x, p1, e1);
-    two_prod(z.hi.y, z.hi.y, p2, e2);
-    two_sum(p1, p2, s, e);
-    float t = __fadd_rn(__fadd_rn(e, e1), e2);
-    t = fmaf(2.f * z.hi.x, z.lo.x, t);
-    t = fmaf(2.f * z.hi.y, z.lo.y, t);
-    df_norm(s, t);  // |z|^2 = s + t
-    const float r0 = __fdiv_rn(1.f, s);
-    float pr, pe;
-    two_prod(s, r0, pr, pe);
-    // residual 1 - (s + t) r0; 1 - pr is exact (pr is within an ulp of 1)
-    const float res = __fsub_rn(__fsub_rn(__fsub_rn(1.f, pr), pe), __fmul_rn(t, r0));
-    float rh, rl;
-    fast_two_sum(r0, __fmul_rn(r0, res), rh, rl);
-    const dfc zc = dfc_make(make_float2(z.hi.x, -z.hi.y), make_float2(z.lo.x, -z.lo.y));
-    return dfc_mul(zc, dfc_make(make_float2(rh, 0.f), make_float2(rl, 0.f)));
-}
-
 // split cluster barrier (release on arrive, acquire on wait); every thread
 // alternates arrive and wait, and cluster.sync() is one arrive plus one wait
 __device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }

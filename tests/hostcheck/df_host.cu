@@ -36,3 +36,13 @@ extern "C" void host_split_d(const double* x, float* out, int n) {
         out[2 * i + 1] = s.y;
     }
 }
+
+// out = 1 / z for a complex df value (re_hi, im_hi, re_lo, im_lo): the pivot
+// reciprocal of the Gauss-Jordan Newton kernels
+extern "C" void host_dfc_inv(const float* z, float* out) {
+    const float4 p = dfc_pack(dfc_inv(dfc_unpack(make_float4(z[0], z[1], z[2], z[3]))));
+    out[0] = p.x;
+    out[1] = p.y;
+    out[2] = p.z;
+    out[3] = p.w;
+}

@@ -4,10 +4,12 @@ rational arithmetic.
 Pass B of the Gram-Schmidt step, the deflation projections, the
 recombination y = Q g and the Newton-Schulz products all accumulate complex
 sums sum_k q_k g_k with q and g stored as FP32 hi + lo pairs (dfacc_mac), and
-the Newton-Schulz update forms c - a b in the same arithmetic (dfc_fms). This
-holds them to their error bounds on the CPU: the split of an FP64 value
-within 2^-48, a length-n accumulation within n 2^-47 of sum |q| |g| (observed
-about sqrt(n) 2^-48), and c - a b within 2^-45 of |a| |b| + |c|."""
+the Newton-Schulz update forms c - a b in the same arithmetic (dfc_fms); the
+Gauss-Jordan Newton kernels divide by their pivots with dfc_inv. This holds
+them to their error bounds on the CPU: the split of an FP64 value within
+2^-48, a length-n accumulation within n 2^-47 of sum |q| |g| (observed about
+sqrt(n) 2^-48), c - a b within 2^-45 of |a| |b| + |c|, and 1 / z within
+2^-44 of |1 / z|."""
 import ctypes
 import os
 import shutil
@@ -37,7 +39,8 @@ def lib():
     L.host_dfacc_dot.argtypes = [P, P, P, P, ctypes.c_int, P]
     L.host_dfc_fms.argtypes = [P, P, P, P]
     L.host_split_d.argtypes = [P, P, ctypes.c_int]
-    for f in (L.host_dfacc_dot, L.host_dfc_fms, L.host_split_d):
+    L.host_dfc_inv.argtypes = [P, P]
+    for f in (L.host_dfacc_dot, L.host_dfc_fms, L.host_split_d, L.host_dfc_inv):
         f.restype = None
     return L
 
@@ -109,3 +112,24 @@ def test_fused_multiply_subtract_against_exact(lib):
         assert float(max(er, ei)) <= 2.0 ** -45 * scale
         # the result is renormalised: the low part is below one unit of the high part
         assert abs(out[2]) <= 2.0 ** -23 * abs(out[0]) + 1e-45 and abs(out[3]) <= 2.0 ** -23 * abs(out[1]) + 1e-45
+
+
+def test_pivot_reciprocal_against_exact(lib):
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    for _ in range(2000):
+        v = rng.standard_normal(2) * np.exp(rng.uniform(-20, 20))
+        if rng.random() < 0.1:  # nearly real or nearly imaginary pivots
+            v[rng.integers(2)] *= 1e-9
+        h, lo = _split(lib, v)
+        z = np.array([h[0], h[1], lo[0], lo[1]], np.float32)
+        out = np.zeros(4, np.float32)
+        lib.host_dfc_inv(z.ctypes.data, out.ctypes.data)
+        zr, zi = _F(z[0]) + _F(z[2]), _F(z[1]) + _F(z[3])
+        n2 = zr * zr + zi * zi
+        xr, xi = zr / n2, -zi / n2  # exact 1 / z
+        mag = float(abs(complex(float(xr), float(xi))))
+        e = float(max(abs(_F(out[0]) + _F(out[2]) - xr), abs(_F(out[1]) + _F(out[3]) - xi)))
+        assert e <= 2.0 ** -44 * mag, (v, e / mag)
+        worst = max(worst, e / mag)
+    assert worst > 0.0  # a double-float result, not an exact one by accident
