@@ -10,6 +10,20 @@
 // converged invariant subspace of B, and keeps the m eigenpairs of A with
 // smallest |Re lambda| (ties: |Im lambda|).
 //
+// Polynomial filter: the wanted eigenvalues of B = A^2 sit at the left end
+// of its spectrum, close to each other compared with the spread of the rest,
+// so plain restarted Arnoldi on B converges slowly. After one unfiltered
+// expansion gives the spread [Re theta_0, |theta|_max] of the Ritz values,
+// the solver restarts on C = T_d(l(B)), a Chebyshev polynomial of degree d in
+// the affine map l that sends the damped interval [a, b] (a: a Ritz value well
+// above the wanted ones, b: above the largest) to [-1, 1]; eigenvalues of B
+// left of a map to |T_d| > 1 and grow like exp(d acosh l), the rest stay in
+// [-1, 1] (Saad, Numerical Methods for Large Eigenvalue Problems, 2nd ed.,
+// Sec. 7.4; Zhou and Saad, J. Comput. Phys. 219 (2006) 172). C has the
+// eigenvectors of B, so the final Rayleigh-Ritz step with A is unchanged.
+// Each application of C is d applications of B by the three-term recurrence
+// y_{i+1} = 2 l(B) y_i - y_{i-1}.
+//
 // Work split: every O(N) operation (stencil, Gram-Schmidt, restart
 // combinations V Z, projections) runs in this library's kernels on the GPU;
 // the O(p^3) projected eigenproblems (p = basis size, at most a few hundred)
@@ -50,6 +64,23 @@ __global__ void k_split_scale(const double2* __restrict__ x, double s, float2* _
         float2 a = split_d(v.x * s), b = split_d(v.y * s);
         hi[i] = make_float2(a.x, b.x);
         lo[i] = make_float2(a.y, b.y);
+    }
+}
+
+// out = sy*y + sz*z + syp*yp (yp may be null): one step of the Chebyshev
+// recurrence with z = B y
+// (out may be yp: each element is read before it is written)
+__global__ void k_cheb(double2* out, const double2* __restrict__ z, const double2* __restrict__ y, const double2* yp,
+                       double sy, double sz, double syp, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double2 a = y[i], b = z[i];
+        double2 r = make_double2(sy * a.x + sz * b.x, sy * a.y + sz * b.y);
+        if (yp) {
+            double2 c = yp[i];
+            r.x += syp * c.x;
+            r.y += syp * c.y;
+        }
+        out[i] = r;
     }
 }
 
@@ -111,6 +142,12 @@ class Solver {
     int G, pstride;
     int restarts = 0, matvecs = 0;
     int power = 2;            // operator B = A^power
+    // Chebyshev filter C = T_d(l(B)), l(z) = (cheb_c - z) / cheb_e; off while cheb_deg == 0.
+    // poly < 0: chosen after the first expansion; 0: never; > 0: that degree
+    int poly = -1, cheb_deg = 0;
+    double cheb_c = 0.0, cheb_e = 1.0, cheb_a = 0.0, cheb_b = 0.0;
+    double2 *cb0 = nullptr, *cb1 = nullptr, *cz = nullptr;
+    void** dslc = nullptr;    // device pointer table {u, tmp, w, cb0, cb1, cz}
     bool start_given = false; // u already holds the start vector (packed FP64)
     bool single = false;      // one expansion only: H of the k-step Arnoldi in Hsingle
     Mat Hsingle;
@@ -152,12 +189,82 @@ class Solver {
         TRYP(Wf = mem.get<double2>(N * (size_t)nev));
         void* hp[4] = {u, tmp, tmp, w};
         OVL_CUDA_TRY(lat, cudaMemcpyAsync(dsl, hp, sizeof hp, cudaMemcpyHostToDevice, st));
+        if (poly != 0 && power == 2) {
+            TRYP(cb0 = mem.get<double2>(N));
+            TRYP(cb1 = mem.get<double2>(N));
+            TRYP(cz = mem.get<double2>(N));
+            TRYP(dslc = mem.get<void*>(6));
+            void* tp[6] = {u, tmp, w, cb0, cb1, cz};
+            OVL_CUDA_TRY(lat, cudaMemcpyAsync(dslc, tp, sizeof tp, cudaMemcpyHostToDevice, st));
+        }
         OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_mu, &mu, sizeof(double), cudaMemcpyHostToDevice, st));
         return OVL_OK;
     }
 
-    // w = B u = A (A u), or A u when power == 1
+    // dst = A (A src) through tmp; indices into dslc {0 u, 1 tmp, 2 w, 3 cb0, 4 cb1, 5 cz}
+    int apply_A2(int src, int dst) {
+        DslashArgs a;
+        a.in = (const void* const*)(dslc + src);
+        a.out = (void* const*)(dslc + 1);
+        a.mu = d_mu;
+        a.nrhs = 1;
+        a.kappa = kappa;
+        if (int rc = ovl_dslash_launch(lat, a, OVL_VEC_F64, OVL_LINKS_F64, st)) return rc;
+        a.in = (const void* const*)(dslc + 1);
+        a.out = (void* const*)(dslc + dst);
+        matvecs++;
+        return ovl_dslash_launch(lat, a, OVL_VEC_F64, OVL_LINKS_F64, st);
+    }
+
+    // w = T_d(l(B)) u by the Chebyshev recurrence (y_0 = u, y_1 = l(B) u,
+    // y_{i+1} = 2 l(B) y_i - y_{i-1}); the iterates rotate through cb0, cb1
+    // (an update may overwrite y_{i-1} in place), B y_i goes to cz
+    int apply_filter() {
+        double2* vec[6] = {u, tmp, w, cb0, cb1, cz};
+        const double ie = 1.0 / cheb_e;
+        int prev = 0, cur = 0;
+        for (int i = 0; i < cheb_deg; i++) {
+            if (int rc = apply_A2(cur, 5)) return rc;
+            const int nxt = (i == cheb_deg - 1) ? 2 : (i == 0 ? 3 : (prev == 0 ? 4 : prev));
+            if (i == 0)
+                k_cheb<<<nblk(lat, N), 256, 0, st>>>(vec[nxt], cz, u, nullptr, cheb_c * ie, -ie, 0.0, N);
+            else
+                k_cheb<<<nblk(lat, N), 256, 0, st>>>(vec[nxt], cz, vec[cur], vec[prev], 2.0 * cheb_c * ie, -2.0 * ie,
+                                                     -1.0, N);
+            OVL_LAUNCH_CHECK(lat);
+            prev = cur;
+            cur = nxt;
+        }
+        return OVL_OK;
+    }
+
+    // Interval [a, b] and degree of the filter from the Ritz values theta of B
+    // of one unfiltered expansion (ascending real parts): b above the largest
+    // |theta|, a at a Ritz value with 2 nev or more below it (for Hermitian B
+    // the i-th Ritz value from the left bounds the i-th eigenvalue from above,
+    // so at least that many eigenvalues lie left of a), d so that
+    // |T_d| reaches about 1e4 at the leftmost Ritz value. Returns false when
+    // the spread gives no useful filter.
+    bool choose_filter(const std::vector<double>& re, double amax) {
+        const int n = (int)re.size();
+        if (n < 4) return false;
+        const int ia = std::min(n - 1, std::max(2 * nev, nev + 20));
+        const double a = re[ia], b = 1.1 * amax, lo = re[0];
+        if (!(a > lo) || !(a < 0.5 * b) || !(lo > -b)) return false;
+        cheb_a = a;
+        cheb_b = b;
+        cheb_c = 0.5 * (a + b);
+        cheb_e = 0.5 * (b - a);
+        const double x0 = (cheb_c - lo) / cheb_e;  // > 1
+        int d = poly > 0 ? poly : (int)ceil(acosh(1e4) / acosh(x0));
+        d = std::max(5, std::min(d, 201));
+        cheb_deg = d | 1;  // odd: an eigenvalue of B right of b (l < -1) gives a large negative T_d, never wanted
+        return true;
+    }
+
+    // w = B u = A (A u), or A u when power == 1; the filtered operator once chosen
     int apply_B() {
+        if (cheb_deg > 0 && power == 2) return apply_filter();
         DslashArgs a;
         a.in = (const void* const*)dsl;
         a.out = (void* const*)(dsl + 1);
@@ -292,7 +399,7 @@ class Solver {
             s.k_used = p - q;
             s.fin = 1;
             OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_sd, &s, sizeof s, cudaMemcpyHostToDevice, st));
-            BatchDev bd;
+            BatchDev bd = {};
             bd.sd = d_sd;
             bd.nsolve = 1;
             bd.N = N;
@@ -325,7 +432,7 @@ class Solver {
             int pc = q + s.k_used;  // columns reached (breakdown: invariant subspace)
             // accurate last-column correction s = Q^dag u and the residual vector
             {
-                ProjDev pd;
+                ProjDev pd = {};
                 pd.qhi = qhi;
                 pd.qlo = qlo;
                 pd.x = u;
@@ -353,28 +460,56 @@ class Solver {
             std::vector<double2*> xs{u};
             if (int rc = dots_many(qhi, qlo, 0, xs, nn)) return rc;
             double beta = sqrt(std::max(0.0, nn(0, 0).real()));
-            // Schur form, wanted = nev smallest Re(theta) first
+            // Schur form, wanted first: the nev smallest Re(theta) of B, or the
+            // nev largest Re(theta) of the filtered operator C
+            const bool filt = cheb_deg > 0;
             Mat T, Z;
             if (!sla::schur(Hp, T, Z)) return ovl_fail(lat, OVL_ENOCONV, "deflation setup: small Schur failed");
             std::vector<int> idx(pc);
             for (int i = 0; i < pc; i++) idx[i] = i;
-            std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return T(a, a).real() < T(b, b).real(); });
+            std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+                return filt ? T(a, a).real() > T(b, b).real() : T(a, a).real() < T(b, b).real();
+            });
             int nw = std::min(nev, pc);
             std::vector<char> want(pc, 0);
             for (int i = 0; i < nw; i++) want[idx[i]] = 1;
+            double amax = 0.0;
+            for (int i = 0; i < pc; i++) amax = std::max(amax, std::abs(T(i, i)));
+            std::vector<double> re_sorted(pc);
+            for (int i = 0; i < pc; i++) re_sorted[i] = T(idx[i], idx[i]).real();
             sla::reorder_schur(T, Z, want);
-            for (int i = 0; i < pc; i++) bnorm = std::max(bnorm, std::abs(T(i, i)));
-            // coupling row b = beta * (last row of Z); converged leading block
+            bnorm = std::max(bnorm, amax);
+            // coupling row b = beta * (last row of Z); converged leading block.
+            // B: |b_i| <= tol |B|; C: |b_i| <= tol |theta_i| (the wanted values of C
+            // span many orders of magnitude, the unwanted ones are at most 1)
             Mat brow(1, pc);
             for (int j = 0; j < pc; j++) brow(0, j) = beta * Z(pc - 1, j);
             int nconv = 0;
             for (int i = 0; i < nw; i++) {
-                if (std::abs(brow(0, i)) <= tol * bnorm)
+                if (std::abs(brow(0, i)) <= tol * (filt ? std::abs(T(i, i)) : bnorm))
                     nconv++;
                 else
                     break;
             }
             bool done = nconv >= nw || pc < p;  // pc < p: exact invariant subspace
+            if (!done && !filt && poly != 0 && power == 2 && choose_filter(re_sorted, amax)) {
+                // switch to C: the Krylov-Schur relation of B does not hold for C,
+                // so restart explicitly from the sum of the wanted Schur vectors
+                Mat Zs(pc, 1);
+                for (int r = 0; r < pc; r++) {
+                    cd s = 0.0;
+                    for (int i = 0; i < nw; i++) s += Z(r, i);
+                    Zs(r, 0) = s;
+                }
+                std::vector<double2*> yu{u};
+                if (int rc = combine(cur_hi, cur_lo, pc, Zs, 1, yu)) return rc;
+                q = 0;
+                Tq = Mat();
+                bq = Mat();
+                bnorm = 0.0;
+                first = true;
+                continue;
+            }
             int qn = done ? nw : std::min(p - 2, nw + std::max((p - nw) / 3, nconv));
             if (qn < 1) qn = 1;
             // new basis columns V Z[:, 0:qn] and the start vector u/beta
@@ -503,6 +638,11 @@ class Solver {
 
 extern "C" int ovl_deflation_setup(ovl_lattice lat, double mu, double m_w, int scheme, int m, double tol,
                                    int max_restarts, ovl_deflation* out) {
+    return ovl_deflation_setup_ex(lat, mu, m_w, scheme, m, tol, max_restarts, -1, out);
+}
+
+extern "C" int ovl_deflation_setup_ex(ovl_lattice lat, double mu, double m_w, int scheme, int m, double tol,
+                                      int max_restarts, int poly_degree, ovl_deflation* out) {
     if (!lat || !out) return ovl_fail(lat, OVL_EINVAL, "ovl_deflation_setup: null argument");
     if (!lat->have_links) return ovl_fail(lat, OVL_EINVAL, "ovl_deflation_setup: links not set");
     if (scheme != OVL_DEFL_SCHUR && scheme != OVL_DEFL_LR)
@@ -529,6 +669,7 @@ extern "C" int ovl_deflation_setup(ovl_lattice lat, double mu, double m_w, int s
     int rc = OVL_OK;
     for (int r = 0; r < runs && !rc; r++) {
         sv[r] = new Solver(lat, r == 0 ? mu : -mu, m_w, p, nev);
+        sv[r]->poly = poly_degree < 0 ? -1 : poly_degree;
         rc = sv[r]->run(tol, max_restarts, 0x9e3779b97f4a7c15ull + r);
         if (!rc) rc = sv[r]->ritz(m, res[r], Gm[r], Mm[r]);
     }
