@@ -1,16 +1,21 @@
 """Benchmark: sgn(H_w(mu)) b solves/s at 1e-8 relative error (and stencil GB/s).
 
-Workload (one "step" = one batched call of the whole hot path): the 8^4
-lattice (N = 49,152), SU(3) links U = exp(i 0.4 X) seed 0, m_w = -1.0,
-mu in {0, 0.1, 0.3, 0.6}, one complex Gaussian source (seed 1) per mu,
-Krylov depth k = 400, m = 30 deflated eigenvectors, Schur and LR deflation:
-8 solves per step, FP64 mode (the mode that reaches 1e-8; the two mixed modes
-floor near 1e-7 and are timed on the same batch under "mixed_precision"). The
-deflation setup (one-off per operator, Sec. 5) runs before the timed region and
-is reported apart.
+Headline workload (one "step" = one batched call of the whole hot path): the
+16^3x32 lattice (N = 1,572,864), SU(3) links U = exp(i 0.3 X) seed 0,
+m_w = -1.2, mu = 0.2, the 12 spin-colour point sources at the origin in one
+batched call, Krylov depth k = 600, Schur deflation with m = 40 critical
+eigenvectors. The deflation setup (GPU Krylov-Schur on A^2 with a Chebyshev
+filter; one-off per operator, Sec. 5) runs before the timed region and is
+reported apart. Arithmetic of the timed form ("df48"): FP64 stencil, Krylov
+basis stored as FP32 hi + lo pairs (48-bit), FP32 products in the pass that
+only steers orthogonality, double-float (48-bit) accumulation in the update
+pass, projections, recombination and Newton. Beside it, on the same inputs:
+the plain FP64 form (complex128 basis, FP64 arithmetic everywhere) and the
+mixed form the workload names (FP32 stencil with 12-real links, complex64
+basis, FP64 coefficients), each with its measured error.
 
-Inputs are synthetic (seeded generators); every step's working set (Krylov
-bases of 8 x 315 MB) is far larger than the 129 MB L2, so no flush is needed.
+Inputs are synthetic (seeded generators); a step's working set (12 Krylov
+bases of 16 GB) is far larger than the 129 MB L2, so no flush is needed.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -20,6 +25,7 @@ Under torchrun (N > 1) every rank runs the same workload on its own GPU
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -31,16 +37,17 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-DIMS = (8, 8, 8, 8)
-EPS, SEED, MW = 0.4, 0, -1.0
-MUS = [0.0, 0.1, 0.3, 0.6]
-K_KRYLOV, M_DEFL = 400, 30
+DIMS, EPS, SEED, MW, MU = (16, 16, 16, 32), 0.3, 0, -1.2, 0.2
+K_KRYLOV, M_DEFL, NSRC = 600, 40, 12
 METRIC = "sgn(H_w(mu)) b solves/s at 1e-8 rel err vs FP64 oracle"
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
-# over the launches of one timed step) from the ncu launch list of this
-# command, profiles/bench_launches_8x4.md; valid while the kernel is unchanged.
-NCU_TRAFFIC = {"gs_pass_b": 1.3725e9, "gs_pass_a": 0.7032e9}
-WORKLOAD = "8^4 eps=0.4 m_w=-1 mu={0,0.1,0.3,0.6} x {Schur,LR} k=400 m=30, FP64 mode"
+WORKLOAD = ("16^3x32 eps=0.3 m_w=-1.2 mu=0.2, 12 spin-colour point sources at the origin in one batched call, "
+            "k=600, Schur m=40 (GPU setup)")
+DTYPE = "df48"
+DTYPE_DETAIL = ("FP64 stencil; Krylov basis as FP32 hi+lo pairs (48-bit); FP32 products in the orthogonality-"
+                "steering pass; double-float (48-bit) accumulation in the update pass, projections and "
+                "recombination; FP64 small-step scalars; double-float Newton")
+# the 8^4 batch of the Schur/LR comparison (reported as an extra)
+DIMS8, EPS8, MW8, MUS8, K8, M8 = (8, 8, 8, 8), 0.4, -1.0, [0.0, 0.1, 0.3, 0.6], 400, 30
 
 
 def peaks():
@@ -107,82 +114,191 @@ def dist_env():
     return ws, rank, local
 
 
-def reference_sketch():
-    path = os.path.join(ROOT, "tests", "golden", "config2_ystar_sketch.json")
-    if not os.path.exists(path):
-        return None
-    return json.load(open(path))
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for key in ("Model name", "BIOS Model name"):
+            m = re.search(rf"^{key}:\s*(.+)$", out, flags=re.M)
+            if m and m.group(1).strip() not in ("-", ""):
+                return m.group(1).strip()
+    except Exception:
+        pass
+    return None
 
 
-def accuracy(y_all, sketch):
-    """Estimated relative error of each solve from the stored probe sketch of y*
+def sources():
+    """The 12 spin-colour point sources at the origin, (spin, colour) order."""
+    return [(s, c) for s in range(4) for c in range(3)]
+
+
+def load_sketch(name):
+    path = os.path.join(ROOT, "tests", "golden", name)
+    return json.load(open(path)) if os.path.exists(path) else None
+
+
+def sketch_error(y, ref, probes):
+    """Estimated relative error of y from a stored probe sketch of y*
     (E|p^dag e|^2 = 2|e|^2 for the complex Gaussian probes)."""
+    sk = np.array(ref["probe_re"]) + 1j * np.array(ref["probe_im"])
+    e = probes.conj() @ np.asarray(y).ravel() - sk
+    return float(np.linalg.norm(e) / np.sqrt(2 * len(sk)) / ref["norm"])
+
+
+def accuracy(ys, sketch, keys):
+    """Per-solve relative error against the oracle sketch (None where the
+    sketch has no entry for that solve); keys[i] names solve i's entry."""
     from paper_0710_0341_gb300 import synth
 
-    if sketch is None:
-        return None
-    P = synth.probe_vectors(12 * 8 ** 4, len(sketch["0.0"]["probe_re"]))
-    out = []
-    for i, y in enumerate(y_all):
-        mu = MUS[i % 4]
-        ref = sketch.get(f"{mu}")
-        if ref is None:
-            out.append(None)
-            continue
-        sk = np.array(ref["probe_re"]) + 1j * np.array(ref["probe_im"])
-        e = P.conj() @ y.ravel() - sk
-        out.append(float(np.linalg.norm(e) / np.sqrt(2 * len(sk)) / ref["norm"]))
-    return out
+    if not sketch:
+        return [None] * len(keys)
+    n = np.asarray(ys[0]).size
+    nprobe = len(next(v for k, v in sketch.items() if not k.startswith("_"))["probe_re"])
+    P = synth.probe_vectors(n, nprobe)
+    return [sketch_error(y, sketch[k], P) if k in sketch else None for y, k in zip(ys, keys)]
 
 
-def cpu_oracle_solve(mu):
-    """One oracle solve of the workload's shape (Schur, k = 400, m = 30) for timing;
-    an orthonormal random block stands in for the Schur vectors (the operation
-    count does not depend on them)."""
-    from oracle import dirac, krylov
-    from paper_0710_0341_gb300 import synth
+def fit_depth_cost(samples, m, k):
+    """Time of a depth-k oracle solve from timed shallower solves: the oracle's
+    step j costs a + c (m + j) (one stencil, and Gram-Schmidt over m + j
+    columns), so T(k) = a k + c (m k + k (k + 1) / 2); a and c by least squares
+    from samples {depth: seconds}."""
+    ks = sorted(samples)
+    M = np.array([[kk, m * kk + kk * (kk + 1) / 2] for kk in ks], float)
+    t = np.array([samples[kk] for kk in ks], float)
+    (a, c), *_ = np.linalg.lstsq(M, t, rcond=None)
+    return float(max(a, 0.0) * k + max(c, 0.0) * (m * k + k * (k + 1) / 2))
 
-    U = synth.random_su3_field(DIMS, EPS, SEED)
-    A = dirac.hermitian_wilson(U, mu, MW)
-    N = A.shape[0]
-    rng = np.random.default_rng(3)
-    S, _ = np.linalg.qr(rng.standard_normal((N, M_DEFL)) + 1j * rng.standard_normal((N, M_DEFL)))
-    T = S.conj().T @ np.column_stack([A @ S[:, i] for i in range(M_DEFL)])
-    b = synth.gaussian_source(DIMS, 1).ravel()
+
+_ORACLE_CASE = {}
+
+
+def oracle_case():
+    """Operator, a stand-in Schur block (orthonormal, T = triu(S^dag A S): the
+    oracle's operation count does not depend on the vectors) and one point
+    source of the headline workload, built once per process."""
+    if not _ORACLE_CASE:
+        from oracle import dirac
+        from paper_0710_0341_gb300 import synth
+
+        U = synth.random_su3_field(DIMS, EPS, SEED)
+        A = dirac.hermitian_wilson(U, MU, MW)
+        N = A.shape[0]
+        rng = np.random.default_rng(3)
+        S, _ = np.linalg.qr(rng.standard_normal((N, M_DEFL)) + 1j * rng.standard_normal((N, M_DEFL)))
+        T = np.triu(S.conj().T @ np.column_stack([A @ S[:, i] for i in range(M_DEFL)]))
+        _ORACLE_CASE.update(A=A, S=S, T=T, b=synth.point_source(DIMS, 0, 0).ravel())
+    return _ORACLE_CASE
+
+
+def oracle_sample(depth):
+    """Seconds of one oracle Schur solve (Eq. 16 on the block matrix, as the
+    oracle restates it) of the headline workload truncated at depth ``depth``."""
+    from oracle import krylov
+
+    c = oracle_case()
     t = time.perf_counter()
-    krylov.sign_schur_block(A, b, K_KRYLOV, S, np.triu(T))
+    krylov.sign_schur_block(c["A"], c["b"], depth, c["S"], c["T"])
     return time.perf_counter() - t
 
 
+def cpu_baseline(depths=(6, 18)):
+    """The oracle on the host cores, bounded: solves at two small depths, their
+    times extrapolated to k = 600 by fit_depth_cost."""
+    oracle_case()
+    samples = {d: oracle_sample(d) for d in depths}
+    t_full = fit_depth_cost(samples, M_DEFL, K_KRYLOV)
+    return {"value": 1.0 / t_full, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": (f"one oracle Schur solve of the workload (point source 0,0; orthonormal stand-in S, m=40) at "
+                       f"depths {list(depths)} ({sum(samples.values()):.1f} s of CPU work), extrapolated to k=600 "
+                       f"by T(k) = a k + c (m k + k(k+1)/2): {t_full:.0f} s per solve"),
+            "sample_seconds": samples, "blas_threads": "all host cores"}
+
+
 def run_reference(args):
+    """The oracle as it stands on the host cores, on this workload's config,
+    metric and unit; each step one bounded sample (alternating depths 6 and
+    18 of one Schur solve), the value extrapolated to the full depth."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        pass  # the CPU oracle needs no warm-up; warm-up steps are empty
-    times = [cpu_oracle_solve(MUS[i % 4]) for i in range(args.steps)]
-    T = sum(times)
-    v = args.steps / T
+    oracle_case()
+    for i in range(args.warmup):
+        oracle_sample((6, 18)[i % 2])
+    per = {6: [], 18: []}
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        d = (6, 18)[i % 2]
+        per[d].append(oracle_sample(d))
+    wall = time.perf_counter() - t0
+    if not per[18]:
+        per[18].append(oracle_sample(18))
+    t_full = fit_depth_cost({d: statistics.mean(v) for d, v in per.items()}, M_DEFL, K_KRYLOV)
+    v = 1.0 / t_full
     cores = os.cpu_count()
     line = {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (one Schur solve per step)", "parallelism": "cpu"},
-            "impl": "reference",
-            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} oracle Schur solves (k=400, m=30, 8^4), one per step"},
+            "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "cpu"}, "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+                             "sample": (f"{args.steps} steps, each one oracle Schur solve of the workload at depth 6 "
+                                        f"or 18 (alternating); the value extrapolates the mean times to k=600 "
+                                        f"({t_full:.0f} s per solve)")},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def roofline(prof, pk, traffic_ratio):
+    """Roofline of the dominant kernel class of one profiled step: algorithmic
+    bytes per launch over its mean launch time, against the measured copy
+    bandwidth; traffic = the ncu DRAM/algorithmic byte ratio of that kernel
+    (committed summary) times its algorithmic bytes per launch."""
+    hbm = pk["hbm_gbs"] if pk else 6800.0
+    dom = max(("gs_pass_b", "gs_pass_a", "stencil"), key=lambda c: prof[c]["ms"])
+    pd = prof[dom]
+    if not pd["launches"]:
+        return None
+    per = pd["bytes"] / pd["launches"]
+    achieved = per / (pd["ms"] / pd["launches"] / 1e3) / 1e9
+    ratio = traffic_ratio.get(dom)
+    return {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": ratio * per if ratio else None, "algorithmic_bytes_per_launch": per,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per algorithmic byte, "
+                              "profiles/gs_pass_b_k_gs_update_16x3x32.md, times this launch's bytes",
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if pk else "fallback 6800 GB/s",
+            "timing": "CUDA events around each launch on the library's stream, one separate profiled step"}
+
+
+def traffic_ratios():
+    """DRAM bytes per algorithmic byte per kernel class from the committed ncu
+    summaries (a line 'traffic_ratio <class> <value>' in each)."""
+    out = {}
+    pdir = os.path.join(ROOT, "profiles")
+    for f in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
+        try:
+            for m in re.finditer(r"^traffic_ratio\s+(\w+)\s+([0-9.eE+-]+)\s*$", open(os.path.join(pdir, f)).read(),
+                                 flags=re.M):
+                out[m.group(1)] = float(m.group(2))
+        except OSError:
+            pass
+    return out
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="headline only (no precision arms, 8^4, stencil)")
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--defl-cache", default=None,
+                    help="deflation data file: loaded when it exists (setup skipped), else written after the setup")
     args = ap.parse_args()
+    if args.cpu_sample:  # child process of the 1-thread CPU baseline
+        print(json.dumps(cpu_baseline()), flush=True)
+        return
     if args.impl == "reference":
         return run_reference(args)
 
@@ -197,23 +313,29 @@ def main():
 
         dist.init_process_group("nccl")
     build.build()
-    dims = DIMS
-    U = synth.random_su3_field(dims, EPS, SEED)
-    h = ovl.ovl_create_lattice(dims, 0, None)
+    U = synth.random_su3_field(DIMS, EPS, SEED)
+    h = ovl.ovl_create_lattice(DIMS, 0, None)
     ovl.ovl_set_links(h, torch.from_numpy(U).cuda())
     # ---- one-off deflation setup (excluded from the metric, reported) ----
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    defl, setup = [], []
-    for scheme in (ovl.OVL_DEFL_SCHUR, ovl.OVL_DEFL_LR):
-        for mu in MUS:
-            ts = time.perf_counter()
-            d = ovl.ovl_deflation_setup(h, mu, MW, scheme, M_DEFL, 1e-12, 3000)
-            setup.append({"scheme": "schur" if scheme == 1 else "lr", "mu": mu, "s": time.perf_counter() - ts,
-                          "restarts_matvecs": ovl.ovl_deflation_stats(d)})
-            defl.append(d)
-    setup_s = time.perf_counter() - t0
-    b = np.stack([synth.gaussian_source(dims, 1)] * 8)
-    params = [dict(mu=mu, m_w=MW, k=K_KRYLOV, prec=ovl.OVL_PREC_FP64) for mu in MUS] * 2
+    if args.defl_cache and os.path.exists(args.defl_cache):
+        d = ovl.ovl_deflation_load(h, args.defl_cache)
+        how = f"loaded from {args.defl_cache} (setup counts of the run that wrote it)"
+    else:
+        d = ovl.ovl_deflation_setup(h, MU, MW, ovl.OVL_DEFL_SCHUR, M_DEFL, 1e-12, 1000)
+        how = "Krylov-Schur on A^2 with a Chebyshev filter (automatic degree), tol 1e-12"
+        if args.defl_cache:
+            ovl.ovl_deflation_save(d, args.defl_cache)
+    torch.cuda.synchronize()
+    setup = {"s": time.perf_counter() - t0, "restarts_A2_applications": ovl.ovl_deflation_stats(d), "method": how}
+    # stencil launch shapes timed on this lattice at the batch's 12 right-hand sides
+    tune = ovl.ovl_autotune(h, NSRC)
+    tuned = {f"{f}/{l}": ovl.ovl_autotune_shape(h, f, l) for f, l in ((0, 0), (1, 1), (1, 2))}
+    srcs = sources()
+    b = np.stack([synth.point_source(DIMS, s, c) for s, c in srcs])
+    params = [dict(mu=MU, m_w=MW, k=K_KRYLOV, prec=ovl.OVL_PREC_FP64)] * NSRC
+    defl = [d] * NSRC
     bd = torch.from_numpy(b).cuda()
     yd = torch.zeros_like(bd)
 
@@ -223,152 +345,191 @@ def main():
     for _ in range(args.warmup):
         infos = step()
     torch.cuda.synchronize()
-    acc = accuracy(yd.cpu().numpy(), reference_sketch())
-    # ---- timed region (device-resident inputs) ----
+    sketch = load_sketch("config3_ystar_sketch.json")
+    keys = [f"{s},{c}" for s, c in srcs]
+    acc = accuracy(list(yd.cpu().numpy()), sketch, keys)
+    # ---- timed region: device-resident inputs, no per-kernel instrumentation ----
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clk = Clocks(local)
     clk.start()
     n0 = ovl.ovl_launch_count(h)
-    ovl.ovl_profile(h, 1)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.nvtx.range_push("timed")  # ncu --nvtx --nvtx-include "timed/" captures these launches only
     ev0.record()
     for _ in range(args.steps):
         infos = step()
     ev1.record()
-    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
-    prof = ovl.ovl_profile(h, 0)
     launches = (ovl.ovl_launch_count(h) - n0) // args.steps
     clocks = clk.stop()
     ms = ev0.elapsed_time(ev1)
-    nsolve = len(params)
-    ms, value = replica_throughput(ms, nsolve * args.steps, ws, "cuda")
+    ms, value = replica_throughput(ms, NSRC * args.steps, ws, "cuda")
+    # ---- one profiled step: per-kernel-class time and the roofline ----
+    ovl.ovl_profile(h, 1)
+    step()
     torch.cuda.synchronize()
-    # ---- end to end through the C ABI with host buffers ----
-    yh = np.zeros_like(b)
-    step_e2e = lambda: ovl.ovl_sign_apply(h, params, defl, b, yh)  # noqa: E731
-    step_e2e()
-    torch.cuda.synchronize()
-    te = time.perf_counter()
-    for _ in range(args.steps):
-        step_e2e()
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - te
-    e2e = {"value": ws * nsolve * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(b.nbytes),
-           "d2h_bytes_per_step": int(yh.nbytes)}
-    # ---- roofline of the dominant kernel class ----
+    prof = ovl.ovl_profile(h, 0)
     pk = peaks()
-    hbm = pk["hbm_gbs"] if pk else 6800.0
-    dom = max(("gs_pass_b", "gs_pass_a", "stencil"), key=lambda c: prof[c]["ms"])
-    pd = prof[dom]
-    achieved = (pd["bytes"] / pd["launches"]) / (pd["ms"] / pd["launches"] / 1e3) / 1e9 if pd["launches"] else None
-    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm if achieved else None, "traffic": NCU_TRAFFIC.get(dom),
-            "traffic_unit": "bytes per launch (ncu)", "algorithmic_bytes_per_launch":
-                pd["bytes"] / pd["launches"] if pd["launches"] else None,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback 6800 GB/s"}
-    breakdown = {c: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
+    roof = roofline(prof, pk, traffic_ratios())
+    breakdown = {c: {"launches": v["launches"], "ms_per_step": v["ms"],
                      "GB_per_s": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 and v["bytes"] > 0 else None}
                  for c, v in prof.items()}
-    # ---- overlap operator D_ov = 1 + gamma5 sgn(H_w) and its adjoint (Eq. 1) on
-    # the LR half of the workload (adjoint deflation data by swapping L and R) ----
-    ovl_meas = None
-    if rank == 0:
-        lr = [d for d, su in zip(defl, setup) if su["scheme"] == "lr"]
-        adj = [ovl.ovl_deflation_adjoint(d) for d in lr]
-        pl = [dict(mu=mu, m_w=MW, k=K_KRYLOV, prec=ovl.OVL_PREC_FP64) for mu in MUS]
-        xo = bd[:4].clone()
-        yo = torch.zeros_like(xo)
-        res = {}
-        for name, dd, adjf in (("D_ov", lr, False), ("D_ov_dagger", adj, True)):
-            ovl.ovl_overlap_apply(h, pl, dd, xo, yo, adjoint=adjf)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            ovl.ovl_overlap_apply(h, pl, dd, xo, yo, adjoint=adjf)
-            e1.record()
-            torch.cuda.synchronize()
-            ms_ov = e0.elapsed_time(e1)
-            res[name] = {"ms_per_call": ms_ov, "applications_per_s": 4 / (ms_ov / 1e3)}
-        for d in adj:
-            ovl.ovl_destroy_deflation(d)
-        ovl_meas = dict(res, config="4 solves (LR, mu in {0,0.1,0.3,0.6}), k=400, m=30, FP64 mode, one call each")
-    # ---- stencil GB/s at 24^3x48 (12-real links, FP32, single rhs, > L2) ----
-    sten = None
-    if rank == 0:
-        sten = stencil_gbs(torch, ovl, synth)
+    # ---- end to end through the C ABI with pinned host buffers ----
+    bh = torch.from_numpy(b).pin_memory()
+    yh = torch.zeros_like(bh).pin_memory()
+    e2e_steps = min(args.steps, 2)
+    ovl.ovl_sign_apply(h, params, defl, bh, yh)
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        ovl.ovl_sign_apply(h, params, defl, bh, yh)
+    e2e_s = time.perf_counter() - te
+    e2e = {"value": ws * NSRC * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(b.nbytes),
+           "d2h_bytes_per_step": int(b.nbytes), "steps": e2e_steps,
+           "host_buffers": "pinned (torch pin_memory), copies inside each call"}
+    del bh, yh
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras["precision_forms"] = guarded(lambda: precision_arms(torch, ovl, h, d, bd, sketch, keys))
+        extras["stencil"] = guarded(lambda: stencil_gbs(torch, ovl, synth))
+        extras["schur_lr_8x4"] = guarded(lambda: extra_8x4(torch, ovl, synth))
+    ovl.ovl_destroy_deflation(d)
+    ovl.ovl_destroy_lattice(h)
     # ---- CPU oracle baseline (rank 0, N = 1) ----
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        t_cpu = cpu_oracle_solve(0.3)
-        cpu = {"value": 1.0 / t_cpu, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "one oracle Schur solve of the workload (mu=0.3, k=400, m=30, 8^4)"}
-    # ---- mixed-precision modes on the same batch (last: a failure here cannot
-    # touch the numbers above) ----
-    mixed = None
+        cpu = guarded(cpu_baseline)
+        one = guarded(lambda: one_thread_baseline())
+        if isinstance(cpu, dict) and isinstance(one, dict):
+            cpu["one_thread"] = {k: one.get(k) for k in ("value", "sample_seconds")}
     if rank == 0:
-        try:
-            mixed = dict(mixed_modes(torch, ovl, h, defl, bd, max(1, args.steps)),
-                         fp64_solves_per_s=value / ws, config="the timed batch, same deflation data")
-        except Exception as e:  # reported, not raised: the line above is already measured
-            mixed = {"error": f"{type(e).__name__}: {e}"[:300]}
-    if rank == 0:
-        ok = [None if a is None else a < 1e-8 for a in acc] if acc else None
+        ok = [None if a is None else a < 1e-8 for a in acc]
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "solves_per_step": nsolve, "parallelism": f"replicas{ws}",
-                           "l2": "working set 2.5 GB >> 129 MB L2, no flush"},
+                "vs_baseline": None, "dtype": DTYPE, "dtype_detail": DTYPE_DETAIL, "data": "synthetic",
+                "config": {"workload": WORKLOAD, "solves_per_step": NSRC, "parallelism": f"replicas{ws}",
+                           "l2": "working set 194 GB >> 129 MB L2, no flush"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks,
-                "accuracy": {"rel_err_est_per_solve": acc, "meets_1e-8": ok,
-                             "reference": "tests/golden/config2_ystar_sketch.json (oracle)"},
-                "newton_iters": [i["newton_iters"] for i in infos],
-                "kernel_breakdown": breakdown, "stencil": sten, "overlap_operator": ovl_meas,
-                "mixed_precision": mixed,
-                "deflation_setup": {"total_s": setup_s, "per_operator": setup,
-                                    "amortised_solves_per_s": amortised(setup_s, ms / args.steps, nsolve)}}
+                "clocks": clocks, "newton_iters": [i["newton_iters"] for i in infos],
+                "deflation_setup": dict(setup, amortised_solves_per_s=amortised(setup["s"], ms / args.steps, NSRC)),
+                "kernel_breakdown_one_step": breakdown,
+                "autotune": {"chosen_tpb_tx_ty_tz": tuned, "candidates_timed": len(tune),
+                             "keys": "fmt/links: 0/0 FP64, 1/1 FP32 18-real, 1/2 FP32 12-real"}}
+        line.update(extras)
+        line["accuracy"] = {"rel_err_per_solve": acc, "meets_1e-8": ok,
+                            "reference": "tests/golden/config3_ystar_sketch.json (oracle y*, probe sketch)"}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
 
 
-def mixed_modes(torch, ovl, h, defl, bd, steps):
-    """The other precision modes on the same batch: solves/s and per-solve
-    error against the oracle sketch. The two mixed modes (FP32 Krylov basis;
-    FP32 links with 18 or 12 reals) floor near 1e-7, so they cannot meet the
-    1e-8 target; the FP64 mode with the double-float stencil keeps the hi + lo
-    basis and can."""
-    sk = reference_sketch()
+def guarded(fn):
+    """Run a measurement that must not touch the numbers already taken: an
+    exception is reported in the line instead of raised."""
+    try:
+        return fn()
+    except Exception as e:
+        return {"error": f"{type(e).__name__}: {e}"[:300]}
+
+
+def one_thread_baseline():
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample"], capture_output=True, text=True,
+                       env=env, timeout=900)
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def precision_arms(torch, ovl, h, d, bd, sketch, keys, plain_sources=2):
+    """The other arithmetic forms on the headline inputs and deflation data,
+    one step each: the plain FP64 form (on the first plain_sources sources:
+    it is bound by the FP64 pipe), the 40-bit basis (BF16 low planes) and the
+    two mixed forms (FP32 stencil with 18-real or 12-real links, complex64
+    basis; all 12 sources). Solves/s and per-solve error against the oracle
+    sketch."""
     out = {}
-    for name, prec in (("fp32_basis_fp32_links", ovl.OVL_PREC_MIXED), ("fp32_basis_r12_links", ovl.OVL_PREC_MIXED_R12),
-                       ("fp64_basis_double_float_stencil", ovl.OVL_PREC_FP64_DFSTENCIL)):
-        pm = [dict(mu=mu, m_w=MW, k=K_KRYLOV, prec=prec) for mu in MUS] * 2
-        y = torch.zeros_like(bd)
-        ovl.ovl_sign_apply(h, pm, defl, bd, y)
+    arms = (("plain_fp64", ovl.OVL_PREC_FP64_PLAIN, plain_sources),
+            ("df40_bf16_low_planes", ovl.OVL_PREC_DF40, NSRC),
+            ("mixed_fp32_basis_r12_links", ovl.OVL_PREC_MIXED_R12, NSRC),
+            ("mixed_fp32_basis_fp32_links", ovl.OVL_PREC_MIXED, NSRC))
+    for name, prec, n in arms:
+        pm = [dict(mu=MU, m_w=MW, k=K_KRYLOV, prec=prec)] * n
+        x = bd[:n].contiguous()
+        y = torch.zeros_like(x)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(steps):
-            ovl.ovl_sign_apply(h, pm, defl, bd, y)
+        ovl.ovl_sign_apply(h, pm, [d] * n, x, y)
         e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
-        err = accuracy(y.cpu().numpy(), sk)
-        meets = None if not err or None in err else all(e < 1e-8 for e in err)
-        out[name] = {"solves_per_s": len(pm) / (ms / 1e3), "ms_per_step": ms, "rel_err_est_per_solve": err,
-                     "meets_1e-8": meets}
+        ms = e0.elapsed_time(e1)
+        err = accuracy(list(y.cpu().numpy()), sketch, keys[:n])
+        known = [e for e in err if e is not None]
+        out[name] = {"solves_per_s": n / (ms / 1e3), "ms_per_step": ms, "solves": n, "rel_err_per_solve": err,
+                     "meets_1e-8": (all(e < 1e-8 for e in known) if known else None)}
+        del x, y
     return out
 
 
+def extra_8x4(torch, ovl, synth):
+    """The 8^4 batch of Schur and LR solves at mu in {0, 0.1, 0.3, 0.6}
+    (k = 400, m = 30, one Gaussian source, 8 solves per call): setup per
+    operator, solves/s, accuracy against its oracle sketch, and the overlap
+    operator D_ov = 1 + gamma5 sgn(H_w) and its adjoint on the LR half."""
+    U = synth.random_su3_field(DIMS8, EPS8, SEED)
+    h = ovl.ovl_create_lattice(DIMS8, 0, None)
+    try:
+        ovl.ovl_set_links(h, torch.from_numpy(U).cuda())
+        defl, setup = [], []
+        for scheme in (ovl.OVL_DEFL_SCHUR, ovl.OVL_DEFL_LR):
+            for mu in MUS8:
+                ts = time.perf_counter()
+                dd = ovl.ovl_deflation_setup(h, mu, MW8, scheme, M8, 1e-12, 3000)
+                setup.append({"scheme": "schur" if scheme == 1 else "lr", "mu": mu, "s": time.perf_counter() - ts,
+                              "restarts_A2_applications": ovl.ovl_deflation_stats(dd)})
+                defl.append(dd)
+        b = np.stack([synth.gaussian_source(DIMS8, 1)] * 8)
+        bd = torch.from_numpy(b).cuda()
+        yd = torch.zeros_like(bd)
+        params = [dict(mu=mu, m_w=MW8, k=K8, prec=ovl.OVL_PREC_FP64) for mu in MUS8] * 2
+        ovl.ovl_sign_apply(h, params, defl, bd, yd)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            ovl.ovl_sign_apply(h, params, defl, bd, yd)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        sk = load_sketch("config2_ystar_sketch.json")
+        err = accuracy(list(yd.cpu().numpy()), sk, [f"{mu}" for mu in MUS8] * 2)
+        res = {"solves_per_s": 8 / (ms / 1e3), "ms_per_step": ms, "rel_err_per_solve": err,
+               "setup_total_s": sum(s["s"] for s in setup), "setup": setup,
+               "config": "8^4 eps=0.4 m_w=-1, mu in {0,0.1,0.3,0.6} x {Schur, LR}, k=400, m=30, df48 mode"}
+        lr = defl[4:]
+        adj = [ovl.ovl_deflation_adjoint(x) for x in lr]
+        pl = params[:4]
+        xo = bd[:4].clone()
+        yo = torch.zeros_like(xo)
+        for name, dd, adjf in (("D_ov", lr, False), ("D_ov_dagger", adj, True)):
+            ovl.ovl_overlap_apply(h, pl, dd, xo, yo, adjoint=adjf)
+            torch.cuda.synchronize()
+            e0.record()
+            ovl.ovl_overlap_apply(h, pl, dd, xo, yo, adjoint=adjf)
+            e1.record()
+            torch.cuda.synchronize()
+            res[name + "_applications_per_s"] = 4 / (e0.elapsed_time(e1) / 1e3)
+        for x in adj + defl:
+            ovl.ovl_destroy_deflation(x)
+        return res
+    finally:
+        ovl.ovl_destroy_lattice(h)
+
+
 def amortised(setup_s, ms_step, nsolve):
-    """Solves/s with the one-off deflation setup of the batch's operators
-    included, for 1 and for 12 sources (spin-colour point sources) per
-    operator: nsolve * s solves over setup + s batches."""
-    return {f"{s}_sources_per_operator": nsolve * s / (setup_s + s * ms_step / 1e3) for s in (1, 12)}
+    """Solves/s with the one-off deflation setup of the batch's operator
+    included, for 1 and for 12 batches per setup: nsolve * s solves over
+    setup + s batches."""
+    return {f"{s}_batches_per_setup": nsolve * s / (setup_s + s * ms_step / 1e3) for s in (1, 12)}
 
 
 def replica_throughput(ms_local, units_local, ws, device):
@@ -414,29 +575,43 @@ def _stencil_case(torch, ovl, synth, dims, nrhs, fmts):
     try:
         ovl.ovl_set_links(h2, torch.from_numpy(synth.random_su3_field(dims, 0.3, 0)).cuda())
         mus = [0.3] * nrhs
+        default = {}
+        for name, fmt, links, sb, lb in fmts:  # the built-in launch shape first
+            default[name] = _time_stencil(torch, ovl, h2, mus, V, nrhs, fmt, links, sb, lb)
+        ovl.ovl_autotune(h2, nrhs)
         for name, fmt, links, sb, lb in fmts:
-            x = torch.randn(12 * V * nrhs, dtype=torch.complex64 if fmt == 1 else torch.complex128, device="cuda")
-            o = torch.zeros_like(x)
-            for _ in range(3):
-                ovl.ovl_apply_Hw_packed(h2, mus, MW, x, o, nrhs, fmt, links)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ovl.ovl_profile(h2, 1)
-            e0.record()
-            n = 20
-            for _ in range(n):
-                ovl.ovl_apply_Hw_packed(h2, mus, MW, x, o, nrhs, fmt, links)
-            e1.record()
-            torch.cuda.synchronize()
-            pr = ovl.ovl_profile(h2, 0)["stencil"]
-            dt = pr["ms"] / pr["launches"] / 1e3  # kernel-only (events around each launch)
-            byt = V * (nrhs * 2 * 12 * sb + 4 * lb)
-            res[name] = {"us_per_launch": dt * 1e6, "GB_per_s": byt / dt / 1e9, "rhs": nrhs,
-                         "bytes_per_site": byt / V, "call_us_incl_host": e0.elapsed_time(e1) / n * 1e3}
-            del x, o
+            r = _time_stencil(torch, ovl, h2, mus, V, nrhs, fmt, links, sb, lb)
+            r["shape_tpb_tx_ty_tz"] = ovl.ovl_autotune_shape(h2, fmt, links)
+            r["builtin_shape"] = {k: default[name][k] for k in ("us_per_launch", "GB_per_s")}
+            res[name] = r
     finally:
         ovl.ovl_destroy_lattice(h2)
     return res
+
+
+def _time_stencil(torch, ovl, h2, mus, V, nrhs, fmt, links, sb, lb):
+    """20 launches of the stencil on packed spinors, timed per launch by the
+    library's events; algorithmic bytes: spinors in and out per right-hand
+    side, the four links of a site once."""
+    x = torch.randn(12 * V * nrhs, dtype=torch.complex64 if fmt == 1 else torch.complex128, device="cuda")
+    o = torch.zeros_like(x)
+    for _ in range(3):
+        ovl.ovl_apply_Hw_packed(h2, mus, MW, x, o, nrhs, fmt, links)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ovl.ovl_profile(h2, 1)
+    e0.record()
+    n = 20
+    for _ in range(n):
+        ovl.ovl_apply_Hw_packed(h2, mus, MW, x, o, nrhs, fmt, links)
+    e1.record()
+    torch.cuda.synchronize()
+    pr = ovl.ovl_profile(h2, 0)["stencil"]
+    dt = pr["ms"] / pr["launches"] / 1e3  # kernel-only (events around each launch)
+    byt = V * (nrhs * 2 * 12 * sb + 4 * lb)
+    del x, o
+    return {"us_per_launch": dt * 1e6, "GB_per_s": byt / dt / 1e9, "rhs": nrhs, "bytes_per_site": byt / V,
+            "call_us_incl_host": e0.elapsed_time(e1) / n * 1e3}
 
 
 if __name__ == "__main__":

@@ -48,11 +48,21 @@ typedef struct ovl_deflation_s*  ovl_deflation;
 
 /* Arithmetic of the Arnoldi path (ovl_sign_params.prec). */
 #define OVL_PREC_FP64       0  /* FP64 stencil; basis stored as FP32 hi+lo pairs (48-bit);
-                                  FP64 Newton, projections and recombination */
+                                  pass-A inner products with FP32 products (they only steer
+                                  orthogonality), pass B, projections and recombination in
+                                  double-float (48-bit) accumulation, FP64 small-step scalars,
+                                  double-float Newton (newton_fp64 = 0) */
 #define OVL_PREC_MIXED      1  /* FP32 stencil (18-real links), FP32 basis, FP64 coefficients */
 #define OVL_PREC_MIXED_R12  2  /* as OVL_PREC_MIXED with 12-real (two-row) links */
 #define OVL_PREC_FP64_DFSTENCIL 3  /* as OVL_PREC_FP64 with the stencil's arithmetic in double-float
                                       (OVL_LINKS_F64DF) on the FP32 pipes */
+#define OVL_PREC_FP64_PLAIN 4  /* plain FP64 throughout: FP64 stencil, complex128 basis, FP64
+                                  products and sums in both Gram-Schmidt passes, the projections and
+                                  the recombination, FP64 Gauss-Jordan Newton (newton_fp64 is
+                                  ignored); the reference form the mixed modes are measured against */
+#define OVL_PREC_DF40       5  /* as OVL_PREC_FP64 with the Krylov columns' low parts stored as BF16
+                                  (FP32 hi + BF16 lo, about 32 significant bits per entry, 12 bytes
+                                  per complex entry instead of 16); deflation vectors keep 48 bits */
 
 /* Deflation scheme (Sec. 3 Schur, Sec. 4 LR). */
 #define OVL_DEFL_NONE   0
@@ -93,6 +103,13 @@ typedef struct {
     int    adapt_every;      /* 0: fixed k */
     int    k_max;            /* upper bound of the adaptive depth (>= k) */
     double tol;              /* target relative error of y (default 1e-8) */
+    /* Schur deflation (one value per batch): 0 (default) sgn of the whole
+     * (m + k) block matrix of Eq. 15 (Eq. 16, which equals Eq. 19 through
+     * Eq. 17); 1 the Sylvester route: sgn(T_m) and sgn(H_k) by the Newton
+     * kernels on the two diagonal blocks, the coupling block Y from the
+     * Sylvester equation of Eq. 18 (FP64, row by row: T_m is triangular),
+     * then Eq. 19. Ignored by LR and undeflated solves. */
+    int    schur_route;
 } ovl_sign_params;
 
 typedef struct {
@@ -174,6 +191,21 @@ int ovl_set_deflation(ovl_lattice lat, double mu, double m_w, int scheme, int m,
  * max_restarts bounds the work (OVL_ENOCONV past it). */
 int ovl_deflation_setup(ovl_lattice lat, double mu, double m_w, int scheme, int m,
                         double tol, int max_restarts, ovl_deflation* out);
+/* ovl_deflation_setup with the caller's choice of polynomial acceleration
+ * (not in the paper, which used ARPACK). After one unfiltered expansion on
+ * A^2 the solver restarts on C = T_d(l(A^2)), the Chebyshev polynomial of odd
+ * degree d in the affine map l that sends the bulk of the spectrum of A^2 (its
+ * Ritz values above the 2 nev-th from the left) to [-1, 1]: the wanted
+ * eigenvalues become the largest of C, by a factor that grows like
+ * exp(d acosh l). C has the eigenvectors of A^2; one application costs d
+ * applications of A^2 (2d stencils), which ovl_deflation_stats counts.
+ * poly_degree < 0: d chosen from the Ritz values (|T_d| about 1e4 at the
+ * leftmost one; this is what ovl_deflation_setup does); 0: plain restarted
+ * Arnoldi on A^2 throughout; > 0: that degree (rounded up to odd, at most 201).
+ * Convergence on C: every wanted Ritz value theta_i of C with
+ * |A^2-coupling b_i| <= tol |theta_i|. */
+int ovl_deflation_setup_ex(ovl_lattice lat, double mu, double m_w, int scheme, int m,
+                           double tol, int max_restarts, int poly_degree, ovl_deflation* out);
 
 /* Copy the deflation data back (canonical layouts as in ovl_set_deflation;
  * L ignored for Schur). Host or device pointers. */
@@ -182,6 +214,18 @@ int ovl_get_deflation(ovl_deflation d, int* scheme, int* m, double* S_or_R, doub
  * restarted Arnoldi runs and applications of A^2 (0 for imported data). */
 int ovl_deflation_stats(ovl_deflation d, int* restarts, int* matvecs);
 int ovl_destroy_deflation(ovl_deflation d);
+
+/* Keep deflation data across processes (not in the paper; Sec. 5 amortises the
+ * one-off eigenvector computation over many evaluations). ovl_deflation_save
+ * writes the vectors (complex128, canonical layout), T or Lambda, mu, m_w, the
+ * setup counts, the lattice dims and boundary and a 64-bit fingerprint of the
+ * links (taken by ovl_set_links), followed by a checksum. ovl_deflation_load
+ * creates a new object (owned by the caller) on lat and returns OVL_EINVAL when
+ * the file is missing, damaged or truncated, or was written for other dims,
+ * another boundary condition or other links. Host files; the data go through
+ * host memory (2 x 16 x N x m bytes for LR). */
+int ovl_deflation_save(ovl_deflation d, const char* path);
+int ovl_deflation_load(ovl_lattice lat, const char* path, ovl_deflation* out);
 
 /* ---- the sign function (Secs. 2-4) ------------------------------------- */
 
@@ -256,6 +300,24 @@ int ovl_ritz_values(ovl_lattice lat, double mu, double m_w, int k, const double*
  * 4 Gram-Schmidt pass B, 5 Newton sign, 6 FP64 projections, 7 recombination. */
 int ovl_launch_count(ovl_lattice lat, long long* n);
 int ovl_profile(ovl_lattice lat, int enable, double* stats);
+
+/* Autotuner of the stencil's launch shape (not in the paper). For the FP32
+ * stencil with 12-real and with 18-real links and the FP64 stencil, times
+ * every candidate shape on this lattice with nrhs right-hand sides (CUDA
+ * events, 5 launches after 2 warm-up launches): 128 consecutive sites per CTA
+ * (and for FP64 also 32), and CTAs covering a tx x ty x tz tile of sites
+ * at one t (x fastest; tx*ty*tz = 128, or 32 for FP64; only tiles that divide
+ * the lattice). The fastest shape per (spinor format, link type) is kept in
+ * the handle and used by every later stencil launch on it (the FP64 shape
+ * also for OVL_LINKS_F64DF); results do not depend on the shape. Allocates
+ * 2 x nrhs complex128 spinors of work space for the call. report (host, may
+ * be NULL): up to max_report records of 7 doubles {fmt, links, tpb, tx, ty,
+ * tz, microseconds per launch}; *n_report (may be NULL) gets their number. */
+int ovl_autotune(ovl_lattice lat, int nrhs, double* report, int max_report, int* n_report);
+/* The shape in use for (fmt OVL_VEC_*, links OVL_LINKS_*): {tpb, tx, ty, tz};
+ * all zero: the built-in rule (consecutive sites, 128 threads; FP64: 32
+ * threads on launches of fewer than 1024 sites per SM). */
+int ovl_autotune_shape(ovl_lattice lat, int fmt, int links, int shape[4]);
 
 /* Failure-detection self test: one CTA waits at a two-member device barrier
  * that nobody else joins, with the same bounded wait the Newton kernel uses

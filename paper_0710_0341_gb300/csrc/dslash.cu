@@ -27,7 +27,21 @@ __device__ __forceinline__ void dslash_site(const KArgs& a) {
         s_w[1] = (T)exp(-mu);
     }
     __syncthreads();
-    const size_t site = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    size_t site;
+    if (a.tx) {  // tiled: block -> (tile x, y, z, t), thread -> site in the tile
+        unsigned b = blockIdx.x;
+        const unsigned nbx = a.Lx / a.tx, nby = a.Ly / a.ty, nbz = a.Lz / a.tz;
+        const unsigned bx = b % nbx;
+        b /= nbx;
+        const unsigned by = b % nby;
+        b /= nby;
+        const unsigned bz = b % nbz, t = b / nbz;
+        const unsigned th = threadIdx.x;
+        const unsigned x = bx * a.tx + th % a.tx, y = by * a.ty + (th / a.tx) % a.ty, z = bz * a.tz + th / (a.tx * a.ty);
+        site = x + (size_t)a.Lx * (y + (size_t)a.Ly * (z + (size_t)a.Lz * t));
+    } else {
+        site = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    }
     if (site >= a.V) return;
     site_compute<T, VT, LINKS>(a, (const VT*)a.in[r], (VT*)a.out[r], site, s_w[0], s_w[1]);
 }
@@ -68,13 +82,22 @@ int ovl_dslash_launch(ovl_lattice lat, const DslashArgs& d, int fmt, int links, 
     a.u32q = lat->links.u32q;
     a.u32r = lat->links.u32r;
     a.u12 = lat->links.u12;
-    dim3 grid((unsigned)((lat->V + 127) / 128), (unsigned)d.nrhs);
+    // launch shape: the autotuner's choice for this format and link type (see
+    // ovl_autotune), else 128 consecutive sites per CTA
+    const OvlStenShape sh = lat->sten_shape[fmt == OVL_VEC_F64 ? 0 : 1][links & 3];
+    a.tx = sh.tx;
+    a.ty = sh.ty;
+    a.tz = sh.tz;
+    const unsigned ntile = sh.tx ? (unsigned)((lat->V / ((size_t)sh.tx * sh.ty * sh.tz))) : 0;
+    dim3 grid(sh.tx ? ntile : (unsigned)((lat->V + 127) / 128), (unsigned)d.nrhs);
+    const int tpb32 = sh.tx ? sh.tx * sh.ty * sh.tz : 128;
     if (fmt == OVL_VEC_F64) {
         // FP64 is bound by the FP64 pipe of each SM: on small launches one-warp
         // CTAs spread the work evenly over the SMs (measured at 8^4 with 8
         // right-hand sides: 62 us per launch with 32 threads, 70 us with 64 or 128)
-        const int tpb = lat->V * (size_t)d.nrhs < (size_t)1024 * lat->num_sms ? 32 : 128;
-        dim3 g64((unsigned)((lat->V + tpb - 1) / tpb), (unsigned)d.nrhs);
+        const int tpb = sh.tx ? tpb32 : sh.tpb ? sh.tpb
+                                               : (lat->V * (size_t)d.nrhs < (size_t)1024 * lat->num_sms ? 32 : 128);
+        dim3 g64(sh.tx ? ntile : (unsigned)((lat->V + tpb - 1) / tpb), (unsigned)d.nrhs);
         if (links == OVL_LINKS_F64DF)  // same shapes as FP64 (at 8^4 x 8 rhs: 81 us with 32 or 128 threads)
             k_dslash<dd, double2, OVL_LINKS_F64><<<g64, tpb, 0, st>>>(a);
         else if (links == OVL_LINKS_F64)
@@ -87,9 +110,9 @@ int ovl_dslash_launch(ovl_lattice lat, const DslashArgs& d, int fmt, int links, 
         if (links == OVL_LINKS_F64 || links == OVL_LINKS_F64DF)
             return ovl_fail(lat, OVL_ENOTSUP, "F32 spinors with F64 links are not built");
         else if (links == OVL_LINKS_F32)
-            k_dslash32<float, float2, OVL_LINKS_F32><<<grid, 128, 0, st>>>(a);
+            k_dslash32<float, float2, OVL_LINKS_F32><<<grid, tpb32, 0, st>>>(a);
         else
-            k_dslash32<float, float2, OVL_LINKS_R12><<<grid, 128, 0, st>>>(a);
+            k_dslash32<float, float2, OVL_LINKS_R12><<<grid, tpb32, 0, st>>>(a);
     }
     OVL_LAUNCH_CHECK(lat);
     return OVL_OK;

@@ -111,6 +111,10 @@ struct KArgs {
     const int* klim;
     int stride, j;
     int Lx, Ly, Lz, Lt;
+    // site tiling of a CTA: tx x ty x tz sites (x fastest) at one t, so that
+    // the neighbour spinors a CTA reads are mostly loaded by the CTA itself
+    // (L1 hits); tx == 0: consecutive site indices per CTA
+    int tx, ty, tz;
     size_t V;
     double kappa;
     int apbc;

@@ -19,6 +19,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include "df.cuh"
 #include "krylov.cuh"
 
@@ -37,6 +39,18 @@ __device__ __forceinline__ double warp_sumd(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Low planes in BF16 (the 40-bit basis): one __nv_bfloat162 (4 bytes) per
+// complex entry; two consecutive rows are one 8-byte load.
+__device__ __forceinline__ float4 lo16_pair(const void* base, size_t r2) {  // rows 2 r2, 2 r2 + 1
+    const uint2 v = __ldg((const uint2*)base + r2);
+    const float2 a = __bfloat1622float2(*(const __nv_bfloat162*)&v.x);
+    const float2 b = __bfloat1622float2(*(const __nv_bfloat162*)&v.y);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float2 lo16_one(const void* base, size_t r) {
+    return __bfloat1622float2(__ldg((const __nv_bfloat162*)base + r));
 }
 
 __device__ __forceinline__ int solve_p(const SolveDev& d, int j) { return j < 0 ? d.m_q + d.k_used : d.m_q + j - 1; }
@@ -333,6 +347,10 @@ __global__ void __launch_bounds__(256) k_gs_small(BatchDev B, int j) {
         float2 sx = split_d(g.x), sy = split_d(g.y);
         d.gh[c] = make_float2(sx.x, sy.x);
         d.gl[c] = make_float2(sx.y, sy.y);
+        if (d.ap64) {
+            d.ap64[c] = cscale(av, inv_nu);
+            d.g64[c] = g;
+        }
     }
 }
 
@@ -358,6 +376,7 @@ __global__ void __launch_bounds__(SR_THREADS) k_gs_small_rows(BatchDev B, int j)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double2* dots = d.dots;
     __shared__ float2 red[SR_THREADS / 32][SR_ROWS];
+    __shared__ double2 red64[SR_THREADS / 32][SR_ROWS];
     __shared__ double sh_r[SR_THREADS / 32];
     __shared__ double2 sh_c[SR_THREADS / 32];
     __shared__ double sh_nu, sh_inv, sh_ep_r, sh_ep_i;
@@ -379,6 +398,15 @@ __global__ void __launch_bounds__(SR_THREADS) k_gs_small_rows(BatchDev B, int j)
             }
         }
         red[warp][lane] = acc;
+        if (B.f64) {  // plain FP64 form: d = H a in FP64 from the FP64 H
+            double2 a64 = make_double2(0.0, 0.0);
+            if (row < p)
+                for (int c = warp; c < p; c += SR_THREADS / 32) {
+                    if (c < cmin) continue;
+                    a64 = cadd(a64, cmul(d.H[row + (size_t)c * ld], dots[c]));
+                }
+            red64[warp][lane] = a64;
+        }
     }
     // |a|^2 and a^dag b (same order in every CTA)
     double aa = 0.0;
@@ -449,6 +477,9 @@ __global__ void __launch_bounds__(SR_THREADS) k_gs_small_rows(BatchDev B, int j)
             dr.x += red[w][lane].x;
             dr.y += red[w][lane].y;
         }
+        double2 dr64 = red64[0][lane];
+        if (B.f64)
+            for (int w = 1; w < SR_THREADS / 32; w++) dr64 = cadd(dr64, red64[w][lane]);
         if (c < p) {
             const double2 av = dots[c];
             // column p-1 += reorthogonalisation coefficients (on breakdown the
@@ -463,7 +494,7 @@ __global__ void __launch_bounds__(SR_THREADS) k_gs_small_rows(BatchDev B, int j)
             if (!stop) {
                 const double inv_nu = sh_inv, epr = sh_ep_r, epi = sh_ep_i;
                 const double2 bv = dots[p + c];
-                const double2 dv = make_double2(dr.x, dr.y);
+                const double2 dv = B.f64 ? dr64 : make_double2(dr.x, dr.y);
                 d.dvec[c] = dv;
                 const double2 cc = make_double2((bv.x - dv.x) * inv_nu, (bv.y - dv.y) * inv_nu);
                 d.H[c + (size_t)p * ld] = cc;
@@ -476,6 +507,10 @@ __global__ void __launch_bounds__(SR_THREADS) k_gs_small_rows(BatchDev B, int j)
                 const float2 sx = split_d(g.x), sy = split_d(g.y);
                 d.gh[c] = make_float2(sx.x, sy.x);
                 d.gl[c] = make_float2(sx.y, sy.y);
+                if (d.ap64) {
+                    d.ap64[c] = cscale(av, inv_nu);
+                    d.g64[c] = g;
+                }
             }
         }
     }
@@ -501,8 +536,9 @@ __global__ void __launch_bounds__(SR_THREADS) k_gs_small_rows(BatchDev B, int j)
 // ---------------------------------------------------------------------------
 // pass B: q_{p+1} and u_{j+1} (see the file header)
 // ---------------------------------------------------------------------------
-template <bool DF>
-__global__ void __launch_bounds__(256) k_gs_update(BatchDev B, int j) {
+template <int LO>  // 0: no low plane; 1: FP32 low planes; 2: BF16 low planes of the Krylov columns
+__global__ void __launch_bounds__(256, 3) k_gs_update(BatchDev B, int j) {
+    constexpr bool DF = LO > 0;
     const int s = blockIdx.y;
     const SolveDev& d = B.sd[s];
     if (!solve_in_step(d, j)) return;
@@ -530,7 +566,8 @@ __global__ void __launch_bounds__(256) k_gs_update(BatchDev B, int j) {
     const double inv_nu = d.scal[0];
     const double2 cu = make_double2(d.scal[1], d.scal[2]);
     float2* qh_out = (float2*)(p < nptr ? d.qhi[p] : d.vhi + (size_t)(p - nptr) * N);
-    float2* ql_out = DF ? (float2*)(p < nptr ? d.qlo[p] : d.vlo + (size_t)(p - nptr) * N) : nullptr;
+    float2* ql_out = LO == 1 ? (float2*)(p < nptr ? d.qlo[p] : d.vlo + (size_t)(p - nptr) * N) : nullptr;
+    __nv_bfloat162* ql16_out = LO == 2 ? (__nv_bfloat162*)d.vlo + (size_t)(p - nptr) * N : nullptr;
     __syncthreads();
     for (size_t base = (size_t)blockIdx.x * UPD_RB; base < N; base += (size_t)gridDim.x * UPD_RB) {
         const bool full = base + UPD_RB <= N;
@@ -551,13 +588,21 @@ __global__ void __launch_bounds__(256) k_gs_update(BatchDev B, int j) {
                 const float4* __restrict__ qh =
                     c >= 0 ? (const float4*)(c < nptr ? s_qh[c] : d.vhi + (size_t)(c - nptr) * N) : nullptr;
                 const float4* __restrict__ ql =
-                    (DF && c >= 0) ? (const float4*)(c < nptr ? s_ql[c] : d.vlo + (size_t)(c - nptr) * N) : nullptr;
+                    (LO == 1 && c >= 0) ? (const float4*)(c < nptr ? s_ql[c] : d.vlo + (size_t)(c - nptr) * N)
+                    : (LO == 2 && c >= 0 && c < nptr) ? (const float4*)s_ql[c] : nullptr;
+                const void* ql16 = (LO == 2 && c >= nptr) ? (const void*)((const __nv_bfloat162*)d.vlo +
+                                                                          (size_t)(c - nptr) * N)
+                                                          : nullptr;
 #pragma unroll
                 for (int i = 0; i < UPD_RPL / 2; i++) {
                     size_t r = base + 64 * i + 2 * lane;
                     bool ok = qh && (full || r < N);
                     h4[bb][i] = ok ? __ldg(qh + (r >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    l4[bb][i] = (DF && ok) ? __ldg(ql + (r >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (LO == 2)
+                        l4[bb][i] = !ok ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                        : ql16 ? lo16_pair(ql16, r >> 1) : __ldg(ql + (r >> 1));
+                    else
+                        l4[bb][i] = (DF && ok) ? __ldg(ql + (r >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
 #pragma unroll
@@ -622,7 +667,8 @@ __global__ void __launch_bounds__(256) k_gs_update(BatchDev B, int j) {
                                           wr.y * inv_nu + (cu.x * ur.y + cu.y * ur.x) - sgv.y);
                 float2 qx = split_d(q.x), qy = split_d(q.y);
                 qh_out[r] = make_float2(qx.x, qy.x);
-                if (DF) ql_out[r] = make_float2(qx.y, qy.y);
+                if (LO == 1) ql_out[r] = make_float2(qx.y, qy.y);
+                if (LO == 2) ql16_out[r] = __floats2bfloat162_rn(qx.y, qy.y);
                 d.u[r] = un;
             }
         }
@@ -668,7 +714,9 @@ __global__ void __launch_bounds__(256) k_proj_dot(ProjDev* pds, double2* part, i
             const float4* __restrict__ qh = (const float4*)d.qhi[c] + (base >> 1);
             // columns without a low plane (FP32 basis) have a null entry: offset only real planes
             const float2* const qlc = d.qlo ? d.qlo[c] : nullptr;
-            const float4* __restrict__ ql = qlc ? (const float4*)qlc + (base >> 1) : nullptr;
+            const bool l16 = c >= d.lo16_from && c < d.lo16_to;  // BF16 low plane (40-bit basis)
+            const float4* __restrict__ ql = (qlc && !l16) ? (const float4*)qlc + (base >> 1) : nullptr;
+            const void* ql16 = (qlc && l16) ? (const void*)((const __nv_bfloat162*)qlc + base) : nullptr;
             dfacc a;
             dfacc_zero(a);
 #pragma unroll
@@ -679,7 +727,9 @@ __global__ void __launch_bounds__(256) k_proj_dot(ProjDev* pds, double2* part, i
                     const int rl = 64 * (hb * (PJ_FL / 2) + i) + 2 * lane;
                     const bool on = full || base + rl < N;
                     hv[i] = on ? __ldg(qh + (rl >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    lv[i] = on && ql ? __ldg(ql + (rl >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    lv[i] = on && ql     ? __ldg(ql + (rl >> 1))
+                            : on && ql16 ? lo16_pair(ql16, rl >> 1)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
 #pragma unroll
                 for (int i = 0; i < PJ_FL / 2; i++) {
@@ -780,7 +830,7 @@ __global__ void __launch_bounds__(256) k_gemv(GemvDev* gds, size_t N) {
         for (int c = 0; c < d.ncol; c++) {
             float2 h = d.qhi[c][r];
             const float2* lp = d.qlo[c];
-            float2 l = lp ? lp[r] : make_float2(0.f, 0.f);
+            float2 l = !lp ? make_float2(0.f, 0.f) : (c >= d.lo16_from && c < d.lo16_to) ? lo16_one(lp, r) : lp[r];
             dfacc_mac(acc, h, l, gh[c], gl[c]);
         }
         d.y[r] = dfacc_value(acc);
@@ -788,7 +838,7 @@ __global__ void __launch_bounds__(256) k_gemv(GemvDev* gds, size_t N) {
 }
 
 // start vector: v1 = x/beta into column m_q and u
-template <bool DF>
+template <int LO>  // as k_gs_update
 __global__ void __launch_bounds__(256) k_start(BatchDev B, const double* beta2, int stride) {
     const int s = blockIdx.y;
     SolveDev& d = B.sd[s];
@@ -805,15 +855,257 @@ __global__ void __launch_bounds__(256) k_start(BatchDev B, const double* beta2, 
     double inv = 1.0 / sqrt(b2);
     const int c0 = d.m_q;
     float2* qh = (float2*)(c0 < d.nptr ? d.qhi[c0] : d.vhi + (size_t)(c0 - d.nptr) * B.N);
-    float2* ql = DF ? (float2*)(c0 < d.nptr ? d.qlo[c0] : d.vlo + (size_t)(c0 - d.nptr) * B.N) : nullptr;
+    float2* ql = LO == 1 ? (float2*)(c0 < d.nptr ? d.qlo[c0] : d.vlo + (size_t)(c0 - d.nptr) * B.N) : nullptr;
+    __nv_bfloat162* ql16 = LO == 2 ? (__nv_bfloat162*)d.vlo + (size_t)(c0 - d.nptr) * B.N : nullptr;
     for (size_t r = blockIdx.x * (size_t)256 + threadIdx.x; r < B.N; r += (size_t)gridDim.x * 256) {
         double2 x = d.u[r];
         double2 v = make_double2(x.x * inv, x.y * inv);
         float2 a = split_d(v.x), b = split_d(v.y);
         qh[r] = make_float2(a.x, b.x);
-        if (DF) ql[r] = make_float2(a.y, b.y);
-        // u_1 must be the stored 48-bit value in the FP64 mode, the stored FP32 value otherwise
-        d.u[r] = DF ? make_double2((double)a.x + (double)a.y, (double)b.x + (double)b.y) : make_double2(a.x, b.x);
+        if (LO == 1) ql[r] = make_float2(a.y, b.y);
+        // u_1 must be the stored value: 48-bit (FP32 low plane), 40-bit (BF16 low plane) or FP32
+        if (LO == 2) {
+            const __nv_bfloat162 l = __floats2bfloat162_rn(a.y, b.y);
+            ql16[r] = l;
+            const float2 lf = __bfloat1622float2(l);
+            d.u[r] = make_double2((double)a.x + (double)lf.x, (double)b.x + (double)lf.y);
+        } else {
+            d.u[r] = LO == 1 ? make_double2((double)a.x + (double)a.y, (double)b.x + (double)b.y)
+                             : make_double2(a.x, b.x);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Plain FP64 form: the same passes on a complex128 basis with FP64 products
+// and FP64 sums throughout (no FP32 storage, no double-float arithmetic).
+// Column c of a solve is (const double2*)qhi[c] for c < nptr, else
+// (const double2*)vhi + (c - nptr) N. GB300 issues FP64 at about 2 FMA per
+// clock and SM, so these kernels are bound by the FP64 pipe (8 FMA per
+// 16-byte basis entry in each pass), not by HBM.
+// ---------------------------------------------------------------------------
+constexpr int D64_RB = 256;  // rows per block of the FP64 inner-product passes
+
+__device__ __forceinline__ const double2* col64(const SolveDev& d, const double2* const* sq, int c, size_t N) {
+    return c < d.nptr ? sq[c] : (const double2*)d.vhi + (size_t)(c - d.nptr) * N;
+}
+
+// pass A: a = Q^dag u, b = Q^dag w, |u|^2, u^dag w, |w|^2 (partials per CTA)
+__global__ void __launch_bounds__(256) k_gs_dot64(BatchDev B, int j) {
+    const int s = blockIdx.y;
+    const SolveDev& d = B.sd[s];
+    if (!solve_in_step(d, j)) return;
+    const int p = solve_p(d, j);
+    const size_t N = B.N;
+    const int CG = gridDim.z, cg = blockIdx.z;
+    __shared__ double2 acc[2 * OVL_MAXCOL + 3];
+    __shared__ const double2* s_col[OVL_MAXPTR];
+    __shared__ double2 s_u[D64_RB], s_w[D64_RB];
+    __shared__ double s_sc[8][4];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int o = tid; o < 2 * p + 3; o += 256) acc[o] = make_double2(0.0, 0.0);
+    if (lane == 0)
+        for (int q = 0; q < 4; q++) s_sc[warp][q] = 0.0;
+    for (int c = tid; c < d.nptr && c < p; c += 256) s_col[c] = (const double2*)d.qhi[c];
+    for (size_t base = (size_t)blockIdx.x * D64_RB; base < N; base += (size_t)gridDim.x * D64_RB) {
+        __syncthreads();
+        {
+            const size_t r = base + tid;
+            const double2 a = r < N ? d.u[r] : make_double2(0.0, 0.0);
+            const double2 b = r < N ? d.w[r] : make_double2(0.0, 0.0);
+            s_u[tid] = a;
+            s_w[tid] = b;
+            if (cg == 0) {
+                double uu = cabs2(a), ww = cabs2(b);
+                double2 uw = cconjmul(a, b);
+                uu = warp_sumd(uu);
+                ww = warp_sumd(ww);
+                uw.x = warp_sumd(uw.x);
+                uw.y = warp_sumd(uw.y);
+                if (lane == 0) {
+                    s_sc[warp][0] += uu;
+                    s_sc[warp][1] += uw.x;
+                    s_sc[warp][2] += uw.y;
+                    s_sc[warp][3] += ww;
+                }
+            }
+        }
+        __syncthreads();
+        for (int c = cg + CG * warp; c < p; c += CG * 8) {
+            const double2* __restrict__ q = col64(d, s_col, c, N) + base;
+            double2 ea = make_double2(0.0, 0.0), eb = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int i = 0; i < D64_RB / 32; i++) {
+                const int rl = 32 * i + lane;
+                if (base + rl < N) {
+                    const double2 qv = __ldg(q + rl);
+                    ea = cadd(ea, cconjmul(qv, s_u[rl]));
+                    eb = cadd(eb, cconjmul(qv, s_w[rl]));
+                }
+            }
+            ea.x = warp_sumd(ea.x);
+            ea.y = warp_sumd(ea.y);
+            eb.x = warp_sumd(eb.x);
+            eb.y = warp_sumd(eb.y);
+            if (lane == 0) {
+                acc[c] = cadd(acc[c], ea);
+                acc[p + c] = cadd(acc[p + c], eb);
+            }
+        }
+    }
+    __syncthreads();
+    if (cg == 0 && tid == 0) {
+        double t[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < 8; w++)
+            for (int q = 0; q < 4; q++) t[q] += s_sc[w][q];
+        acc[2 * p] = make_double2(t[0], 0.0);
+        acc[2 * p + 1] = make_double2(t[1], t[2]);
+        acc[2 * p + 2] = make_double2(t[3], 0.0);
+    }
+    __syncthreads();
+    double2* out = B.part + ((size_t)s * B.G + blockIdx.x) * B.pstride;
+    for (int c = cg + CG * tid; c < p; c += CG * 256) {
+        out[c] = acc[c];
+        out[p + c] = acc[p + c];
+    }
+    if (cg == 0 && tid < 3) out[2 * p + tid] = acc[2 * p + tid];
+}
+
+// pass B: q_{p+1} = u/nu - Q (a/nu) -> column p; u <- w/nu - (e_p/nu) u - Q g
+__global__ void __launch_bounds__(256) k_gs_update64(BatchDev B, int j) {
+    const int s = blockIdx.y;
+    const SolveDev& d = B.sd[s];
+    if (!solve_in_step(d, j)) return;
+    const int p = solve_p(d, j);
+    const size_t N = B.N;
+    extern __shared__ double2 upd64_dyn[];  // ap (pmax), g (pmax), then column pointers
+    double2* s_ap = upd64_dyn;
+    double2* s_g = s_ap + B.pmax;
+    const double2** s_col = (const double2**)(s_g + B.pmax);
+    for (int c = threadIdx.x; c < p; c += 256) {
+        s_ap[c] = d.ap64[c];
+        s_g[c] = d.g64[c];
+    }
+    for (int c = threadIdx.x; c < d.nptr && c < p; c += 256) s_col[c] = (const double2*)d.qhi[c];
+    const double inv_nu = d.scal[0];
+    const double2 cu = make_double2(d.scal[1], d.scal[2]);
+    double2* q_out = (double2*)(p < d.nptr ? (const double2*)d.qhi[p] : (const double2*)d.vhi + (size_t)(p - d.nptr) * N);
+    __syncthreads();
+    for (size_t r = blockIdx.x * (size_t)256 + threadIdx.x; r < N; r += (size_t)gridDim.x * 256) {
+        double2 sq = make_double2(0.0, 0.0), sg = make_double2(0.0, 0.0);
+        int c = 0;
+        for (; c + 4 <= p; c += 4) {  // four loads in flight
+            double2 qv[4];
+#pragma unroll
+            for (int t = 0; t < 4; t++) qv[t] = __ldg(col64(d, s_col, c + t, N) + r);
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                sq = cadd(sq, cmul(qv[t], s_ap[c + t]));
+                sg = cadd(sg, cmul(qv[t], s_g[c + t]));
+            }
+        }
+        for (; c < p; c++) {
+            const double2 qv = __ldg(col64(d, s_col, c, N) + r);
+            sq = cadd(sq, cmul(qv, s_ap[c]));
+            sg = cadd(sg, cmul(qv, s_g[c]));
+        }
+        const double2 ur = d.u[r], wr = d.w[r];
+        q_out[r] = csub(cscale(ur, inv_nu), sq);
+        d.u[r] = csub(cadd(cscale(wr, inv_nu), cmul(cu, ur)), sg);
+    }
+}
+
+// P[c] = Q[:,c]^dag x (c < ncol) and |x|^2, partials per CTA
+__global__ void __launch_bounds__(256) k_proj_dot64(ProjDev* pds, double2* part, int G, int pstride, size_t N) {
+    const int s = blockIdx.y;
+    const ProjDev d = pds[s];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ double2 acc[OVL_MAXCOL + 1];
+    __shared__ double2 s_x[D64_RB];
+    __shared__ double s_nn[8];
+    for (int o = tid; o <= d.ncol; o += 256) acc[o] = make_double2(0.0, 0.0);
+    if (lane == 0) s_nn[warp] = 0.0;
+    for (size_t base = (size_t)blockIdx.x * D64_RB; base < N; base += (size_t)gridDim.x * D64_RB) {
+        __syncthreads();
+        const size_t r = base + tid;
+        const double2 x = r < N ? d.x[r] : make_double2(0.0, 0.0);
+        s_x[tid] = x;
+        const double nn = warp_sumd(cabs2(x));
+        if (lane == 0) s_nn[warp] += nn;
+        __syncthreads();
+        for (int c = warp; c < d.ncol; c += 8) {
+            const double2* __restrict__ q = (const double2*)d.qhi[c] + base;
+            double2 e = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int i = 0; i < D64_RB / 32; i++) {
+                const int rl = 32 * i + lane;
+                if (base + rl < N) e = cadd(e, cconjmul(__ldg(q + rl), s_x[rl]));
+            }
+            e.x = warp_sumd(e.x);
+            e.y = warp_sumd(e.y);
+            if (lane == 0) acc[c] = cadd(acc[c], e);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; w++) t += s_nn[w];
+        acc[d.ncol] = make_double2(t, 0.0);
+    }
+    __syncthreads();
+    double2* out = part + ((size_t)s * G + blockIdx.x) * pstride;
+    for (int o = tid; o <= d.ncol; o += 256) out[o] = acc[o];
+}
+
+// x -= sum_c Q[:,c] coef[c]
+__global__ void __launch_bounds__(256) k_proj_update64(ProjDev* pds, size_t N) {
+    const int s = blockIdx.y;
+    const ProjDev d = pds[s];
+    __shared__ double2 co[OVL_MAXCOL];
+    for (int c = threadIdx.x; c < d.ncol; c += 256) co[c] = d.coef[c];
+    __syncthreads();
+    for (size_t r = blockIdx.x * (size_t)256 + threadIdx.x; r < N; r += (size_t)gridDim.x * 256) {
+        double2 v = make_double2(0.0, 0.0);
+        for (int c = 0; c < d.ncol; c++) v = cadd(v, cmul(__ldg((const double2*)d.qhi[c] + r), co[c]));
+        d.x[r] = csub(d.x[r], v);
+    }
+}
+
+// y = sum_c Q[:,c] g[c]
+__global__ void __launch_bounds__(256) k_gemv64(GemvDev* gds, size_t N) {
+    const int s = blockIdx.y;
+    const GemvDev d = gds[s];
+    __shared__ double2 co[OVL_MAXCOL + 64];
+    for (int c = threadIdx.x; c < d.ncol; c += 256) co[c] = d.g[c];
+    __syncthreads();
+    for (size_t r = blockIdx.x * (size_t)256 + threadIdx.x; r < N; r += (size_t)gridDim.x * 256) {
+        double2 v = make_double2(0.0, 0.0);
+        for (int c = 0; c < d.ncol; c++) v = cadd(v, cmul(__ldg((const double2*)d.qhi[c] + r), co[c]));
+        d.y[r] = v;
+    }
+}
+
+// v_1 = x / beta into column m_q (complex128) and into u
+__global__ void __launch_bounds__(256) k_start64(BatchDev B, const double* beta2, int stride) {
+    const int s = blockIdx.y;
+    SolveDev& d = B.sd[s];
+    if (!d.active) return;
+    const double b2 = beta2[(size_t)s * stride];
+    if (!(b2 > 0.0)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            d.active = 0;
+            d.k_used = 0;
+            d.fin = 0;
+        }
+        return;
+    }
+    const double inv = 1.0 / sqrt(b2);
+    const int c0 = d.m_q;
+    double2* q = (double2*)(c0 < d.nptr ? (const double2*)d.qhi[c0] : (const double2*)d.vhi + (size_t)(c0 - d.nptr) * B.N);
+    for (size_t r = blockIdx.x * (size_t)256 + threadIdx.x; r < B.N; r += (size_t)gridDim.x * 256) {
+        const double2 v = cscale(d.u[r], inv);
+        q[r] = v;
+        d.u[r] = v;
     }
 }
 
@@ -850,7 +1142,10 @@ int ovl_gs_dot(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
         }
     }
     dim3 grid(b.G, b.nsolve, cgs);
-    k_gs_dot<<<grid, DOT_THREADS, 0, st>>>(b, j);
+    if (b.f64)
+        k_gs_dot64<<<grid, 256, 0, st>>>(b, j);
+    else
+        k_gs_dot<<<grid, DOT_THREADS, 0, st>>>(b, j);
     OVL_LAUNCH_CHECK(lat);
     return OVL_OK;
 }
@@ -882,16 +1177,26 @@ int ovl_gs_update(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
     // the batch is homogeneous in precision (checked by the caller)
     size_t dyn = (size_t)b.pmax * 3 * sizeof(float2) + 2 * OVL_MAXPTR * sizeof(void*);
     if (!lat->gs_update_attr) {  // a function attribute of the lattice's device
-        OVL_CUDA_TRY(lat, cudaFuncSetAttribute(k_gs_update<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        OVL_CUDA_TRY(lat, cudaFuncSetAttribute(k_gs_update<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                64 * 1024));
-        OVL_CUDA_TRY(lat, cudaFuncSetAttribute(k_gs_update<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        OVL_CUDA_TRY(lat, cudaFuncSetAttribute(k_gs_update<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               64 * 1024));
+        OVL_CUDA_TRY(lat, cudaFuncSetAttribute(k_gs_update<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                64 * 1024));
         lat->gs_update_attr = true;
     }
-    if (b.df)
-        k_gs_update<true><<<grid, 256, dyn, st>>>(b, j);
+    if (b.f64) {
+        const size_t dyn64 = (size_t)b.pmax * 2 * sizeof(double2) + OVL_MAXPTR * sizeof(void*);
+        if (dyn64 > 48 * 1024)
+            OVL_CUDA_TRY(lat, cudaFuncSetAttribute(k_gs_update64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)dyn64));
+        k_gs_update64<<<grid, 256, dyn64, st>>>(b, j);
+    } else if (b.lo16)
+        k_gs_update<2><<<grid, 256, dyn, st>>>(b, j);
+    else if (b.df)
+        k_gs_update<1><<<grid, 256, dyn, st>>>(b, j);
     else
-        k_gs_update<false><<<grid, 256, dyn, st>>>(b, j);
+        k_gs_update<0><<<grid, 256, dyn, st>>>(b, j);
     OVL_LAUNCH_CHECK(lat);
     return OVL_OK;
 }
@@ -902,14 +1207,18 @@ int ovl_gs_final(ovl_lattice lat, const BatchDev& b, ProjDev* pd_dev, int maxcol
     // the basis orthonormal to ~1e-7 only; the Arnoldi relation itself is
     // exact, and with an accurate s the projected matrix equals
     // Q^+ A Q, i.e. the result is the Galerkin approximation on span(Q)).
-    if (int rc = ovl_proj_dot(lat, pd_dev, b.nsolve, maxcol, b.part, b.G, st)) return rc;
+    if (int rc = ovl_proj_dot(lat, pd_dev, b.nsolve, maxcol, b.part, b.G, st, b.f64)) return rc;
     return ovl_gs_small(lat, b, -1, st);
 }
 
-int ovl_proj_dot(ovl_lattice lat, ProjDev* pd_dev, int nsolve, int maxcol, double2* part, int G, cudaStream_t st) {
+int ovl_proj_dot(ovl_lattice lat, ProjDev* pd_dev, int nsolve, int maxcol, double2* part, int G, cudaStream_t st,
+                 int f64) {
     int pstride = maxcol + 1;
     dim3 grid(G, nsolve);
-    k_proj_dot<<<grid, 256, 0, st>>>(pd_dev, part, G, pstride, lat->N);
+    if (f64)
+        k_proj_dot64<<<grid, 256, 0, st>>>(pd_dev, part, G, pstride, lat->N);
+    else
+        k_proj_dot<<<grid, 256, 0, st>>>(pd_dev, part, G, pstride, lat->N);
     OVL_LAUNCH_CHECK(lat);
     dim3 g2((maxcol + 1 + 31) / 32, nsolve);
     k_proj_reduce<<<g2, 256, 0, st>>>(pd_dev, part, G, pstride);
@@ -917,24 +1226,30 @@ int ovl_proj_dot(ovl_lattice lat, ProjDev* pd_dev, int nsolve, int maxcol, doubl
     return OVL_OK;
 }
 
-int ovl_proj_update(ovl_lattice lat, ProjDev* pd_dev, int nsolve, int maxcol, cudaStream_t st) {
+int ovl_proj_update(ovl_lattice lat, ProjDev* pd_dev, int nsolve, int maxcol, cudaStream_t st, int f64) {
     (void)maxcol;
     size_t blocks = (lat->N + 255) / 256;
     size_t g = (size_t)lat->num_sms * 4;
     if (blocks < g) g = blocks;
     dim3 grid((unsigned)g, nsolve);
-    k_proj_update<<<grid, 256, 0, st>>>(pd_dev, lat->N);
+    if (f64)
+        k_proj_update64<<<grid, 256, 0, st>>>(pd_dev, lat->N);
+    else
+        k_proj_update<<<grid, 256, 0, st>>>(pd_dev, lat->N);
     OVL_LAUNCH_CHECK(lat);
     return OVL_OK;
 }
 
-int ovl_gemv_df(ovl_lattice lat, GemvDev* gd_dev, int nsolve, int maxcol, cudaStream_t st) {
+int ovl_gemv_df(ovl_lattice lat, GemvDev* gd_dev, int nsolve, int maxcol, cudaStream_t st, int f64) {
     (void)maxcol;
     size_t blocks = (lat->N + 255) / 256;
     size_t g = (size_t)lat->num_sms * 4;
     if (blocks < g) g = blocks;
     dim3 grid((unsigned)g, nsolve);
-    k_gemv<<<grid, 256, 0, st>>>(gd_dev, lat->N);
+    if (f64)
+        k_gemv64<<<grid, 256, 0, st>>>(gd_dev, lat->N);
+    else
+        k_gemv<<<grid, 256, 0, st>>>(gd_dev, lat->N);
     OVL_LAUNCH_CHECK(lat);
     return OVL_OK;
 }
@@ -944,10 +1259,14 @@ int ovl_start_vector(ovl_lattice lat, const BatchDev& b, const double* beta2_dev
     size_t g = (size_t)lat->num_sms * 4;
     if (blocks < g) g = blocks;
     dim3 grid((unsigned)g, b.nsolve);
-    if (b.df)
-        k_start<true><<<grid, 256, 0, st>>>(b, beta2_dev, beta_stride);
+    if (b.f64)
+        k_start64<<<grid, 256, 0, st>>>(b, beta2_dev, beta_stride);
+    else if (b.lo16)
+        k_start<2><<<grid, 256, 0, st>>>(b, beta2_dev, beta_stride);
+    else if (b.df)
+        k_start<1><<<grid, 256, 0, st>>>(b, beta2_dev, beta_stride);
     else
-        k_start<false><<<grid, 256, 0, st>>>(b, beta2_dev, beta_stride);
+        k_start<0><<<grid, 256, 0, st>>>(b, beta2_dev, beta_stride);
     OVL_LAUNCH_CHECK(lat);
     return OVL_OK;
 }

@@ -33,6 +33,11 @@ struct SolveDev {
     float2* gh;      // pass-B coefficients g, high part    (FP32)
     float2* gl;      // pass-B coefficients g, low part     (FP32)
     double* scal;    // [0] 1/nu, [1..2] -e_p/nu (complex), [3] nu, [4] beta_k
+    // plain FP64 form only (null otherwise): the pass-B coefficients in FP64,
+    // a/nu in ap64[0..p) and g in g64[0..p); the basis columns then hold
+    // double2 values (qhi[c] and vhi point to complex128 data, qlo/vlo unused)
+    double2* ap64;
+    double2* g64;
     int m_q;         // leading fixed columns (Schur vectors)
     int k;           // requested Krylov depth
     int ldH;
@@ -51,6 +56,9 @@ struct BatchDev {
     int pstride;     // >= 2*OVL_MAXCOL + 3
     int pmax;        // max over solves of the basis columns used at this step
     int df;          // FP64 mode: basis has low planes
+    int f64;         // plain FP64 form: complex128 basis, FP64 products everywhere
+    int lo16;        // 40-bit basis: the Krylov columns' low planes are BF16 (vlo holds
+                     // __nv_bfloat162 entries); the Schur columns keep FP32 low planes
 };
 
 // launchers (krylov.cu)
@@ -70,9 +78,13 @@ struct ProjDev {
     double2* out;              // ncol + 1 results
     const double2* coef;       // for the update: x -= sum_c Q[:,c] coef[c]
     int ncol;
+    int f64;                   // columns are complex128 (qhi entries point to double2 data)
+    int lo16_from, lo16_to;    // columns in [from, to) have BF16 low planes (empty: from = to = 0)
 };
-int ovl_proj_dot(ovl_lattice lat, ProjDev* pd_dev, int nsolve, int maxcol, double2* part, int G, cudaStream_t st);
-int ovl_proj_update(ovl_lattice lat, ProjDev* pd_dev, int nsolve, int maxcol, cudaStream_t st);
+// f64: the columns are complex128 (plain FP64 form); else hi (+ lo) FP32 planes
+int ovl_proj_dot(ovl_lattice lat, ProjDev* pd_dev, int nsolve, int maxcol, double2* part, int G, cudaStream_t st,
+                 int f64 = 0);
+int ovl_proj_update(ovl_lattice lat, ProjDev* pd_dev, int nsolve, int maxcol, cudaStream_t st, int f64 = 0);
 int ovl_gs_final(ovl_lattice lat, const BatchDev& b, ProjDev* pd_dev, int maxcol, cudaStream_t st);
 
 // y_s = sum_c Q_s[:,c] g_s[c] (df accumulation), FP64 packed output.
@@ -82,8 +94,10 @@ struct GemvDev {
     const double2* g;
     double2* y;
     int ncol;
+    int f64;                   // columns are complex128 (qhi entries point to double2 data)
+    int lo16_from, lo16_to;    // columns in [from, to) have BF16 low planes (empty: from = to = 0)
 };
-int ovl_gemv_df(ovl_lattice lat, GemvDev* gd_dev, int nsolve, int maxcol, cudaStream_t st);
+int ovl_gemv_df(ovl_lattice lat, GemvDev* gd_dev, int nsolve, int maxcol, cudaStream_t st, int f64 = 0);
 
 // v_1 = x / beta into column m_q of Q (split hi/lo) and into u.
 int ovl_start_vector(ovl_lattice lat, const BatchDev& b, const double* beta2_dev, int beta_stride,

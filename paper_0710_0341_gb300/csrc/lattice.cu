@@ -134,6 +134,24 @@ __global__ void k_links_convert(const double2* __restrict__ Uc, size_t V, double
             make_float4((float)e[2 * p].x, (float)e[2 * p].y, (float)e[2 * p + 1].x, (float)e[2 * p + 1].y);
 }
 
+// 64-bit fingerprint of the FP64 link field: the sum (mod 2^64) over its
+// doubles of a SplitMix64 mix of (bits + index * golden ratio), so that the
+// same field gives the same value on any launch shape; used to tie saved
+// deflation data to the links they were computed for.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+__global__ void k_link_hash(const double* __restrict__ u, size_t n, unsigned long long* out) {
+    unsigned long long acc = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        acc += mix64((unsigned long long)__double_as_longlong(u[i]) + i * 0x9e3779b97f4a7c15ull);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
 extern "C" int ovl_set_links(ovl_lattice lat, const double* U) {
     if (!lat || !U) return ovl_fail(lat, OVL_EINVAL, "ovl_set_links: null argument");
     size_t V = lat->V;
@@ -164,6 +182,15 @@ extern "C" int ovl_set_links(ovl_lattice lat, const double* U) {
     k_links_convert<<<nb, 256, 0, lat->stream>>>(src, V, lat->links.u64, lat->links.u32q, lat->links.u32r,
                                                   lat->links.u12);
     OVL_LAUNCH_CHECK(lat);
+    {
+        void* p;
+        if (int rc = ovl_scratch(lat, bytes + sizeof(unsigned long long), &p)) return rc;
+        unsigned long long* hd = (unsigned long long*)((char*)p + bytes);  // after the staged links
+        OVL_CUDA_TRY(lat, cudaMemsetAsync(hd, 0, sizeof *hd, lat->stream));
+        k_link_hash<<<(unsigned)lat->num_sms * 4, 256, 0, lat->stream>>>((const double*)lat->links.u64, V * 4 * 18, hd);
+        OVL_LAUNCH_CHECK(lat);
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(&lat->link_hash, hd, sizeof *hd, cudaMemcpyDeviceToHost, lat->stream));
+    }
     OVL_CUDA_TRY(lat, cudaStreamSynchronize(lat->stream));
     lat->have_links = true;
     return OVL_OK;

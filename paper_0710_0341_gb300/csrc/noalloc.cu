@@ -34,6 +34,10 @@ static int noalloc_base(ovl_lattice lat, unsigned char** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128)
         return ovl_fail(lat, OVL_ECUDA, "ovl_apply_Hw_noalloc: no current device");
+    // the address looked up is that of the current device's copy of the array
+    if (dev != lat->device)
+        return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw_noalloc: current device %d is not the lattice's device %d",
+                        dev, lat->device);
     std::lock_guard<std::mutex> g(g_noalloc_mu);
     if (!g_noalloc_addr[dev]) {
         void* p = nullptr;

@@ -39,6 +39,12 @@ struct LinkSet {
     float4*  u12 = nullptr;
 };
 
+// Stencil launch shape: tx x ty x tz sites per CTA (tx = 0: consecutive
+// sites, tpb threads per CTA, tpb = 0: the built-in rule)
+struct OvlStenShape {
+    int tpb = 0, tx = 0, ty = 0, tz = 0;
+};
+
 struct ovl_lattice_s {
     int dims[4];       // Lx, Ly, Lz, Lt
     int apbc;          // antiperiodic in t
@@ -47,6 +53,7 @@ struct ovl_lattice_s {
     int device;
     LinkSet links;
     bool have_links = false;
+    unsigned long long link_hash = 0;  // fingerprint of the FP64 links (ovl_set_links)
     std::string err;
     // device status word for kernels that can time out or fail (int[64])
     int* d_status = nullptr;
@@ -60,6 +67,8 @@ struct ovl_lattice_s {
     // per-device launch facts of this lattice's device, found on first use
     int gs_dot_occ = 0;            // resident pass-A CTAs per SM
     bool gs_update_attr = false;   // pass B may take more than 48 KB of shared memory
+    // stencil launch shapes per [spinor format F64/F32][link type], set by ovl_autotune
+    OvlStenShape sten_shape[2][4];
     // kernels launched by this handle, and optional per-class event timing
     long long launches = 0;
     bool prof = false;
@@ -93,6 +102,10 @@ struct ovl_deflation_s {
     float2* S_lo = nullptr;
     float2* L_hi = nullptr;   // LR only
     float2* L_lo = nullptr;
+    // complex128 copies for the plain FP64 form: exact for imported vectors,
+    // built from hi + lo on first use otherwise
+    double2* S64 = nullptr;
+    double2* L64 = nullptr;
     double2* T = nullptr;     // Schur: m x m column-major (device); LR: Lambda (m)
     std::vector<double> T_host;  // same data on the host (2*m*m or 2*m doubles)
     int setup_restarts = 0;      // restarts and operator applications of ovl_deflation_setup

@@ -19,6 +19,7 @@
 #include "df.cuh"
 #include "krylov.cuh"
 #include "newton.cuh"
+#include "sylvester.cuh"
 
 // Newton-Schulz takes over from the scaled Newton iteration once a step is
 // below NS_SWITCH (relative, Frobenius); at most NS_MAX_ITER products steps
@@ -73,7 +74,7 @@ unsigned grid_for(size_t n, int sms) {
 // ---------------------------------------------------------------------------
 // deflation data
 // ---------------------------------------------------------------------------
-static int upload_vectors(ovl_lattice lat, const double* canon, int m, float2** hi, float2** lo) {
+static int upload_vectors(ovl_lattice lat, const double* canon, int m, float2** hi, float2** lo, double2** f64) {
     size_t N = lat->N;
     size_t vb = N * sizeof(double2) * (size_t)m;
     if (cudaMalloc(hi, N * sizeof(float2) * m) != cudaSuccess || cudaMalloc(lo, N * sizeof(float2) * m) != cudaSuccess) {
@@ -92,7 +93,31 @@ static int upload_vectors(ovl_lattice lat, const double* canon, int m, float2** 
     if (int rc = ovl_pack_impl(lat, src, packed, m, OVL_VEC_F64, lat->stream)) return rc;
     k_split_planes<<<grid_for(N * m, lat->num_sms), 256, 0, lat->stream>>>(packed, *hi, *lo, N * m);
     OVL_LAUNCH_CHECK(lat);
+    if (cudaMalloc(f64, vb) != cudaSuccess) {
+        cudaGetLastError();
+        return ovl_fail(lat, OVL_ENOMEM, "deflation vectors: allocation failed");
+    }
+    OVL_CUDA_TRY(lat, cudaMemcpyAsync(*f64, packed, vb, cudaMemcpyDeviceToDevice, lat->stream));
     OVL_CUDA_TRY(lat, cudaStreamSynchronize(lat->stream));
+    return OVL_OK;
+}
+
+// complex128 copies of the deflation vectors for the plain FP64 form, joined
+// from the hi + lo planes when the object has none yet (computed or adjoint data)
+static int defl_fp64(ovl_lattice lat, ovl_deflation d) {
+    const size_t N = lat->N, n = N * (size_t)d->m;
+    for (int which = 0; which < 2; which++) {
+        double2** dst = which ? &d->L64 : &d->S64;
+        const float2* hi = which ? d->L_hi : d->S_hi;
+        const float2* lo = which ? d->L_lo : d->S_lo;
+        if (*dst || !hi) continue;
+        if (cudaMalloc(dst, n * sizeof(double2)) != cudaSuccess) {
+            cudaGetLastError();
+            return ovl_fail(lat, OVL_ENOMEM, "deflation vectors: FP64 copy does not fit");
+        }
+        k_join_planes<<<grid_for(n, lat->num_sms), 256, 0, lat->stream>>>(hi, lo, *dst, n);
+        OVL_LAUNCH_CHECK(lat);
+    }
     return OVL_OK;
 }
 
@@ -103,6 +128,8 @@ extern "C" int ovl_destroy_deflation(ovl_deflation d) {
     cudaFree(d->S_lo);
     cudaFree(d->L_hi);
     cudaFree(d->L_lo);
+    cudaFree(d->S64);
+    cudaFree(d->L64);
     cudaFree(d->T);
     delete d;
     return OVL_OK;
@@ -122,8 +149,8 @@ extern "C" int ovl_set_deflation(ovl_lattice lat, double mu, double m_w, int sch
     d->m = m;
     d->mu = mu;
     d->m_w = m_w;
-    int rc = upload_vectors(lat, S_or_R, m, &d->S_hi, &d->S_lo);
-    if (!rc && scheme == OVL_DEFL_LR) rc = upload_vectors(lat, L, m, &d->L_hi, &d->L_lo);
+    int rc = upload_vectors(lat, S_or_R, m, &d->S_hi, &d->S_lo, &d->S64);
+    if (!rc && scheme == OVL_DEFL_LR) rc = upload_vectors(lat, L, m, &d->L_hi, &d->L_lo, &d->L64);
     if (rc) {
         ovl_destroy_deflation(d);
         return rc;
@@ -153,15 +180,22 @@ extern "C" int ovl_set_deflation(ovl_lattice lat, double mu, double m_w, int sch
     return OVL_OK;
 }
 
-static int download_vectors(ovl_lattice lat, const float2* hi, const float2* lo, int m, double* canon) {
+// packed vectors -> canonical (host or device); from the exact complex128
+// copy when the object has one, else from the hi + lo planes (48-bit)
+static int download_vectors(ovl_lattice lat, const float2* hi, const float2* lo, const double2* f64, int m,
+                            double* canon) {
     size_t N = lat->N;
     size_t vb = N * sizeof(double2) * (size_t)m;
     void* s;
     if (int rc = ovl_scratch(lat, 2 * vb, &s)) return rc;
     double2* packed = (double2*)s;
     double2* cdev = (double2*)((char*)s + vb);
-    k_join_planes<<<grid_for(N * m, lat->num_sms), 256, 0, lat->stream>>>(hi, lo, packed, N * m);
-    OVL_LAUNCH_CHECK(lat);
+    if (f64) {
+        OVL_CUDA_TRY(lat, cudaMemcpyAsync(packed, f64, vb, cudaMemcpyDeviceToDevice, lat->stream));
+    } else {
+        k_join_planes<<<grid_for(N * m, lat->num_sms), 256, 0, lat->stream>>>(hi, lo, packed, N * m);
+        OVL_LAUNCH_CHECK(lat);
+    }
     bool dev = ovl_is_device_ptr(canon);
     if (int rc = ovl_unpack_impl(lat, packed, dev ? canon : (double*)cdev, m, OVL_VEC_F64, lat->stream)) return rc;
     if (!dev) OVL_CUDA_TRY(lat, cudaMemcpyAsync(canon, cdev, vb, cudaMemcpyDeviceToHost, lat->stream));
@@ -175,9 +209,9 @@ extern "C" int ovl_get_deflation(ovl_deflation d, int* scheme, int* m, double* S
     if (scheme) *scheme = d->scheme;
     if (m) *m = d->m;
     if (S_or_R)
-        if (int rc = download_vectors(lat, d->S_hi, d->S_lo, d->m, S_or_R)) return rc;
+        if (int rc = download_vectors(lat, d->S_hi, d->S_lo, d->S64, d->m, S_or_R)) return rc;
     if (L && d->scheme == OVL_DEFL_LR)
-        if (int rc = download_vectors(lat, d->L_hi, d->L_lo, d->m, L)) return rc;
+        if (int rc = download_vectors(lat, d->L_hi, d->L_lo, d->L64, d->m, L)) return rc;
     if (T) {
         size_t tb = d->T_host.size() * sizeof(double);
         if (ovl_is_device_ptr(T))
@@ -208,6 +242,9 @@ struct SolvePlan {
     double2 *dots = nullptr, *dvec = nullptr;
     float2 *ap = nullptr, *gh = nullptr, *gl = nullptr;
     double* scal = nullptr;
+    double2 *ap64 = nullptr, *g64 = nullptr;
+    // Sylvester route (Schur, Eqs. 18-19): sgn(H_k) copy, R, Y, work, sgn(T) S^dag b
+    double2 *syFH = nullptr, *syR = nullptr, *syY = nullptr, *syW = nullptr, *syr = nullptr, *sygT = nullptr;
     const float2** qhi = nullptr;
     const float2** qlo = nullptr;
     double2 *X = nullptr, *W = nullptr, *Yns = nullptr;
@@ -235,15 +272,23 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     const size_t N = lat->N;
     const int prec = params[0].prec;
     const double m_w = params[0].m_w;
-    if (prec < OVL_PREC_FP64 || prec > OVL_PREC_FP64_DFSTENCIL)
+    if (prec < OVL_PREC_FP64 || prec > OVL_PREC_DF40)
         return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: precision %d unknown", prec);
-    const bool df = prec == OVL_PREC_FP64 || prec == OVL_PREC_FP64_DFSTENCIL;  // hi + lo basis
+    const bool lo16 = prec == OVL_PREC_DF40;  // BF16 low planes of the Krylov columns
+    const bool df = prec == OVL_PREC_FP64 || prec == OVL_PREC_FP64_DFSTENCIL || lo16;  // hi + lo basis
+    const bool f64 = prec == OVL_PREC_FP64_PLAIN;                              // complex128 basis
+    // the plain FP64 form takes the FP64 Gauss-Jordan Newton whatever newton_fp64 says
+    const int nmode = f64 ? 1 : params[0].newton_fp64;
+    const bool syl = params[0].schur_route == 1;  // Schur solves by Eqs. 18-19
     std::vector<SolvePlan> P(nsolve);
     int kmax = 0, ldmax = 0, mdef_max = 0;
     for (int i = 0; i < nsolve; i++) {
         const ovl_sign_params& q = params[i];
         if (q.prec != prec) return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: mixed precisions in one batch");
         if (q.m_w != m_w) return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: one m_w per batch");
+        if (q.schur_route != params[0].schur_route || q.schur_route < 0 || q.schur_route > 1)
+            return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: solve %d: schur_route=%d (0 or 1, one per batch)", i,
+                            q.schur_route);
         if (q.newton_fp64 != params[0].newton_fp64 || q.newton_fp64 < 0 || q.newton_fp64 > 4)
             return ovl_fail(lat, OVL_EINVAL, "ovl_sign_apply: solve %d: newton_fp64=%d (0..4, one per batch)", i,
                             q.newton_fp64);
@@ -290,8 +335,8 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
                 T* q = c.take<std::remove_const_t<T>>(n);
                 if (carve) ptr = q;
             };
-            t(p.Vhi, N * (p.k + 1));
-            if (df) t(p.Vlo, N * (p.k + 1));
+            t(p.Vhi, N * (p.k + 1) * (f64 ? 2 : 1));  // complex128 columns take two float2 slots
+            if (df) t(p.Vlo, lo16 ? (N * (p.k + 1) + 1) / 2 : N * (p.k + 1));  // BF16 pairs: 4 bytes per entry
             t(p.u, N);
             t(p.w, N);
             t(p.H, ld * ld);
@@ -302,6 +347,19 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             t(p.gh, ld);
             t(p.gl, ld);
             t(p.scal, 8);
+            if (f64) {
+                t(p.ap64, ld);
+                t(p.g64, ld);
+            }
+            if (syl && p.m_q) {
+                const size_t kk = (size_t)p.k, mm = (size_t)p.m_q;
+                t(p.syFH, kk * kk);
+                t(p.syR, mm * kk);
+                t(p.syY, mm * kk);
+                t(p.syW, kk * kk);
+                t(p.syr, kk);
+                t(p.sygT, mm);
+            }
             t(p.qhi, ld);
             t(p.qlo, ld);
             t(p.X, nm * nm);
@@ -342,6 +400,7 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         SolveDev *sd = nullptr, *sd_est = nullptr;
         NewtonDev* nd = nullptr;
         NsDev* ns = nullptr;
+        SylDev* sy = nullptr;
         ProjDev* pd = nullptr;
         GemvDev* gd = nullptr;
         double2* part = nullptr;
@@ -357,6 +416,7 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         q.sd_est = cb.take<SolveDev>(nsolve);
         q.nd = cb.take<NewtonDev>(nsolve);
         q.ns = cb.take<NsDev>(nsolve);
+        q.sy = cb.take<SylDev>(nsolve);
         q.pd = cb.take<ProjDev>(nsolve);
         q.gd = cb.take<GemvDev>(nsolve);
         q.part = cb.take<double2>((size_t)nsolve * G * pstride);
@@ -402,6 +462,11 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     for (int i = 0; i < nsolve; i++)
         if (int rc = ovl_pack_impl(lat, bsrc + 2 * N * i, P[i].u, 1, OVL_VEC_F64, st)) return rc;
 
+    if (f64)
+        for (int i = 0; i < nsolve; i++)
+            if (P[i].d)
+                if (int rc = defl_fp64(lat, P[i].d)) return rc;
+
     // ---- column pointers, descriptors ----
     std::vector<SolveDev> hs(nsolve);
     std::vector<const float2*> tmp_hi, tmp_lo;
@@ -410,12 +475,14 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         tmp_hi.assign(p.ldH, nullptr);
         tmp_lo.assign(p.ldH, nullptr);
         for (int cidx = 0; cidx < p.m_q; cidx++) {
-            tmp_hi[cidx] = p.d->S_hi + N * cidx;
-            tmp_lo[cidx] = p.d->S_lo + N * cidx;
+            tmp_hi[cidx] = f64 ? (const float2*)(p.d->S64 + N * cidx) : p.d->S_hi + N * cidx;
+            tmp_lo[cidx] = f64 ? nullptr : p.d->S_lo + N * cidx;
         }
         for (int cidx = p.m_q; cidx < p.ldH; cidx++) {
-            tmp_hi[cidx] = p.Vhi + N * (cidx - p.m_q);
-            tmp_lo[cidx] = df ? p.Vlo + N * (cidx - p.m_q) : nullptr;
+            tmp_hi[cidx] = f64 ? (const float2*)((double2*)p.Vhi + N * (cidx - p.m_q)) : p.Vhi + N * (cidx - p.m_q);
+            tmp_lo[cidx] = !df ? nullptr
+                           : lo16 ? (const float2*)((const char*)p.Vlo + (size_t)4 * N * (cidx - p.m_q))
+                                  : p.Vlo + N * (cidx - p.m_q);
         }
         OVL_CUDA_TRY(lat, cudaMemcpyAsync(p.qhi, tmp_hi.data(), p.ldH * sizeof(void*), cudaMemcpyHostToDevice, st));
         OVL_CUDA_TRY(lat, cudaMemcpyAsync(p.qlo, tmp_lo.data(), p.ldH * sizeof(void*), cudaMemcpyHostToDevice, st));
@@ -436,6 +503,8 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         s.gh = p.gh;
         s.gl = p.gl;
         s.scal = p.scal;
+        s.ap64 = f64 ? p.ap64 : nullptr;
+        s.g64 = f64 ? p.g64 : nullptr;
         s.m_q = p.m_q;
         s.k = p.k;
         s.ldH = p.ldH;
@@ -465,12 +534,13 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             q.ncol = (which == 2 || p.scheme == OVL_DEFL_NONE || (which == 1 && p.scheme != OVL_DEFL_SCHUR)) ? 0 : p.m_defl;
             q.out = which == 0 ? p.pout1 : which == 1 ? p.pout2 : p.pout3;
             q.qhi = p.pc_hi;
-            q.qlo = p.pc_lo;
+            q.qlo = f64 ? nullptr : p.pc_lo;
             q.coef = q.out;
+            q.f64 = f64;
             maxcol = std::max(maxcol, q.ncol);
         }
         OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_pd, pd.data(), nsolve * sizeof(ProjDev), cudaMemcpyHostToDevice, st));
-        if (int rc = ovl_proj_dot(lat, d_pd, nsolve, maxcol, d_part, G, st)) return rc;
+        if (int rc = ovl_proj_dot(lat, d_pd, nsolve, maxcol, d_part, G, st, f64)) return rc;
         if (which == 2 || maxcol == 0) {
             OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
             return OVL_OK;
@@ -478,10 +548,10 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         // update x -= Q coef with the update columns (S for Schur, R for LR)
         for (int i = 0; i < nsolve; i++) {
             pd[i].qhi = P[i].pu_hi;
-            pd[i].qlo = P[i].pu_lo;
+            pd[i].qlo = f64 ? nullptr : P[i].pu_lo;
         }
         OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_pd, pd.data(), nsolve * sizeof(ProjDev), cudaMemcpyHostToDevice, st));
-        if (int rc = ovl_proj_update(lat, d_pd, nsolve, maxcol, st)) return rc;
+        if (int rc = ovl_proj_update(lat, d_pd, nsolve, maxcol, st, f64)) return rc;
         OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
         return OVL_OK;
     };
@@ -491,6 +561,12 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         std::vector<const float2*> dh(p.m_defl), dl(p.m_defl), uh(p.m_defl), ul(p.m_defl);
         for (int cidx = 0; cidx < p.m_defl; cidx++) {
             bool lr = p.scheme == OVL_DEFL_LR;
+            if (f64) {
+                dh[cidx] = (const float2*)((lr ? p.d->L64 : p.d->S64) + N * cidx);
+                uh[cidx] = (const float2*)(p.d->S64 + N * cidx);
+                dl[cidx] = ul[cidx] = nullptr;
+                continue;
+            }
             dh[cidx] = (lr ? p.d->L_hi : p.d->S_hi) + N * cidx;
             dl[cidx] = (lr ? p.d->L_lo : p.d->S_lo) + N * cidx;
             uh[cidx] = p.d->S_hi + N * cidx;
@@ -528,7 +604,7 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     }
 
     // ---- start vectors ----
-    BatchDev bd;
+    BatchDev bd = {};
     bd.sd = d_sd;
     bd.nsolve = nsolve;
     bd.N = N;
@@ -536,6 +612,8 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     bd.G = G;
     bd.pstride = pstride;
     bd.df = df;
+    bd.f64 = f64;
+    bd.lo16 = lo16;
     bd.pmax = 0;
     // beta^2 sits in .x of pout3[0]; pass it through a per-solve array
     {
@@ -563,13 +641,13 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     da.stride = (int)(sizeof(SolveDev) / sizeof(int));
     da.nrhs = nsolve;
     da.kappa = 1.0 / (8.0 + 2.0 * m_w);
-    const int links = prec == OVL_PREC_FP64             ? OVL_LINKS_F64
+    const int links = (prec == OVL_PREC_FP64 || f64 || lo16) ? OVL_LINKS_F64
                       : prec == OVL_PREC_FP64_DFSTENCIL ? OVL_LINKS_F64DF
                       : prec == OVL_PREC_MIXED          ? OVL_LINKS_F32
                                                         : OVL_LINKS_R12;
     const double site_bytes =
         2.0 * 12 * 16 + 4.0 * ((links == OVL_LINKS_F64 || links == OVL_LINKS_F64DF) ? 144 : links == OVL_LINKS_F32 ? 72 : 48);
-    const double qbytes = df ? 16.0 : 8.0;
+    const double qbytes = lo16 ? 12.0 : (df || f64) ? 16.0 : 8.0;
     bool any_adapt = false;
     for (int i = 0; i < nsolve; i++) any_adapt = any_adapt || P[i].adapt > 0;
     // accurate Galerkin correction of the last column (FP64 projection of u)
@@ -580,11 +658,14 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         for (int i = 0; i < nsolve; i++) {
             ProjDev& q = pd[i];
             q.qhi = P[i].qhi;
-            q.qlo = P[i].qlo;
+            q.qlo = df ? P[i].qlo : nullptr;
             q.x = P[i].u;
             q.out = P[i].dots;
             q.coef = nullptr;
             q.ncol = ncol[i];
+            q.f64 = f64;
+            q.lo16_from = lo16 ? P[i].m_q : 0;  // the Krylov columns
+            q.lo16_to = lo16 ? ncol[i] : 0;
             maxcol = std::max(maxcol, q.ncol);
         }
         OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_pd, pd.data(), nsolve * sizeof(ProjDev), cudaMemcpyHostToDevice, st));
@@ -601,8 +682,11 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     };
     // scaled Newton on H[0:n, 0:n] of each solve with n[i] > 0; g = F c
     std::vector<NewtonDev> nd(nsolve);
+    // cvo (optional): per-solve coefficient vectors c replacing the default
+    // (S^dag b; beta e_1) or beta e_1 (used by the Sylvester route)
     auto newton = [&](const std::vector<const double2*>& Hs, const std::vector<int>& nn,
-                      const std::vector<double2*>& gout) -> int {
+                      const std::vector<double2*>& gout,
+                      const std::vector<std::vector<double2>>* cvo = nullptr) -> int {
         int nmax_run = 0, any_run = 0;
         for (int i = 0; i < nsolve; i++) {
             SolvePlan& p = P[i];
@@ -625,10 +709,10 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             q.iters = p.iters;
             q.cvec = p.cvec;
             q.gout = gout[i];
-            q.df = params[0].newton_fp64 == 1 ? 0 : 1;
+            q.df = nmode == 1 ? 0 : 1;
             q.crow = p.crow;
             q.Wg = (float4*)p.W;
-            q.ns_switch = (params[0].newton_fp64 == 0 || params[0].newton_fp64 == 4) ? NS_SWITCH : 0.0;
+            q.ns_switch = (nmode == 0 || nmode == 4) ? NS_SWITCH : 0.0;
             q.resume = 0;
             q.handoff = p.handoff;
             if (q.run) {
@@ -637,10 +721,14 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             }
             // coefficient vector: Schur (S^dag b; beta e_1), otherwise beta e_1
             std::vector<double2> cv(std::max(1, n), make_double2(0.0, 0.0));
-            if (p.scheme == OVL_DEFL_SCHUR)
-                for (int t = 0; t < p.m_q && t < n; t++)
-                    cv[t] = make_double2(c1[i][t].x + c2[i][t].x, c1[i][t].y + c2[i][t].y);
-            if (n > p.m_q) cv[p.m_q] = make_double2(beta[i], 0.0);
+            if (cvo && !(*cvo)[i].empty()) {
+                for (int t = 0; t < n && t < (int)(*cvo)[i].size(); t++) cv[t] = (*cvo)[i][t];
+            } else {
+                if (p.scheme == OVL_DEFL_SCHUR)
+                    for (int t = 0; t < p.m_q && t < n; t++)
+                        cv[t] = make_double2(c1[i][t].x + c2[i][t].x, c1[i][t].y + c2[i][t].y);
+                if (n > p.m_q) cv[p.m_q] = make_double2(beta[i], 0.0);
+            }
             OVL_CUDA_TRY(lat,
                          cudaMemcpyAsync(p.cvec, cv.data(), std::max(1, n) * sizeof(double2), cudaMemcpyHostToDevice, st));
             OVL_CUDA_TRY(lat, cudaMemsetAsync(p.bar, 0, sizeof(unsigned), st));
@@ -657,7 +745,7 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
             // 1: FP64 Gauss-Jordan; 2: cooperative double-float only; 3: cluster (else
             // cooperative) double-float only; 4: as 0 with every Newton-Schulz step
             // declined (the return to Gauss-Jordan)
-            const int mode = params[0].newton_fp64;
+            const int mode = nmode;
             int cl_size = 0, cl_nrs = 0, cl_l2 = 0, cpm_df = 1, smem_rows = 0;
             size_t cl_smem = 0;
             if (mode == 0 || mode == 3 || mode == 4)
@@ -848,23 +936,105 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
     OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
 
     // ---- small sign by Newton ----
+    std::vector<int> syl_on(nsolve, 0), nit_extra(nsolve, 0);
+    std::vector<int> nstat(nsolve, 0), nit(nsolve, 0);
     {
         std::vector<const double2*> Hs(nsolve);
         std::vector<int> nn(nsolve);
         std::vector<double2*> go(nsolve);
+        std::vector<std::vector<double2>> cvo(nsolve);
         for (int i = 0; i < nsolve; i++) {
-            Hs[i] = P[i].H;
-            nn[i] = hs[i].status == 0 ? P[i].m_q + hs[i].k_used : 0;
-            go[i] = P[i].gcomb;
+            SolvePlan& p = P[i];
+            const int ku = hs[i].status == 0 ? hs[i].k_used : 0;
+            syl_on[i] = syl && p.m_q > 0 && ku > 0;
+            if (syl_on[i]) {  // sgn(H_k) beta e_1 on the Krylov block alone (Eq. 19)
+                Hs[i] = p.H + (size_t)p.m_q * (p.ldH + 1);
+                nn[i] = ku;
+                go[i] = p.gcomb + p.m_q;
+                cvo[i].assign(1, make_double2(beta[i], 0.0));
+            } else {
+                Hs[i] = p.H;
+                nn[i] = hs[i].status == 0 ? p.m_q + ku : 0;
+                go[i] = p.gcomb;
+            }
         }
-        if (int rc = newton(Hs, nn, go)) return rc;
+        if (int rc = newton(Hs, nn, go, &cvo)) return rc;
+        for (int i = 0; i < nsolve; i++) {  // status and iterations of this run (a second run resets them)
+            OVL_CUDA_TRY(lat, cudaMemcpyAsync(&nstat[i], P[i].nstat, sizeof(int), cudaMemcpyDeviceToHost, st));
+            OVL_CUDA_TRY(lat, cudaMemcpyAsync(&nit[i], P[i].iters, sizeof(int), cudaMemcpyDeviceToHost, st));
+        }
+        OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
+        bool any_syl = false;
+        for (int i = 0; i < nsolve; i++) any_syl = any_syl || syl_on[i];
+        if (any_syl) {
+            // keep sgn(H_k), then sgn(T) S^dag b from the Newton kernels on T
+            const std::vector<NewtonDev> nd_first = nd;
+            for (int i = 0; i < nsolve; i++) {
+                if (!syl_on[i]) continue;
+                const size_t kk = (size_t)hs[i].k_used;
+                OVL_CUDA_TRY(lat, cudaMemcpyAsync(P[i].syFH, P[i].X, kk * kk * sizeof(double2),
+                                                  cudaMemcpyDeviceToDevice, st));
+            }
+            int nst = 0;
+            for (int i = 0; i < nsolve; i++)
+                if (syl_on[i] && nstat[i]) nst = nstat[i];
+            for (int i = 0; i < nsolve; i++) {
+                Hs[i] = P[i].H;
+                nn[i] = syl_on[i] ? P[i].m_q : 0;
+                go[i] = P[i].sygT;
+                cvo[i].clear();
+                if (syl_on[i])
+                    for (int t = 0; t < P[i].m_q; t++)
+                        cvo[i].push_back(make_double2(c1[i][t].x + c2[i][t].x, c1[i][t].y + c2[i][t].y));
+            }
+            if (!nst) {
+                if (int rc = newton(Hs, nn, go, &cvo)) return rc;
+                std::vector<SylDev> sy(nsolve);
+                int mmax = 0;
+                for (int i = 0; i < nsolve; i++) {
+                    SylDev& z = sy[i];
+                    memset(&z, 0, sizeof z);
+                    if (!syl_on[i]) continue;
+                    SolvePlan& p = P[i];
+                    z.H = p.H;
+                    z.ldH = p.ldH;
+                    z.m = p.m_q;
+                    z.k = hs[i].k_used;
+                    z.on = 1;
+                    z.df = nmode == 1 ? 0 : 1;
+                    z.FT = p.X;
+                    z.FH = p.syFH;
+                    z.R = p.syR;
+                    z.Y = p.syY;
+                    z.W = p.syW;
+                    z.r = p.syr;
+                    z.gT = p.sygT;
+                    z.gS = p.gcomb;
+                    z.beta = beta[i];
+                    mmax = std::max(mmax, p.m_q);
+                }
+                OVL_CUDA_TRY(lat, cudaMemcpyAsync(bp.sy, sy.data(), nsolve * sizeof(SylDev), cudaMemcpyHostToDevice, st));
+                ProfScope py(lat, 5, 0.0, st);
+                if (int rc = ovl_sylvester_launch(lat, bp.sy, nsolve, mmax, st)) return rc;
+                py.end(st);
+                OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));  // sy must outlive the copy
+                for (int i = 0; i < nsolve; i++) {
+                    if (!syl_on[i]) continue;
+                    int s2 = 0, i2 = 0;
+                    OVL_CUDA_TRY(lat, cudaMemcpy(&s2, P[i].nstat, sizeof(int), cudaMemcpyDeviceToHost));
+                    OVL_CUDA_TRY(lat, cudaMemcpy(&i2, P[i].iters, sizeof(int), cudaMemcpyDeviceToHost));
+                    if (!nstat[i]) nstat[i] = s2;
+                    nit_extra[i] = i2;  // iterations on T, added to those on H_k
+                }
+            }
+            // the recombination below runs over the m + k columns of each solve
+            nd = nd_first;
+            for (int i = 0; i < nsolve; i++)
+                if (syl_on[i]) nd[i].n = P[i].m_q + hs[i].k_used;
+        }
     }
-    std::vector<int> nstat(nsolve, 0), nit(nsolve, 0);
-    for (int i = 0; i < nsolve; i++) {
-        OVL_CUDA_TRY(lat, cudaMemcpyAsync(&nstat[i], P[i].nstat, sizeof(int), cudaMemcpyDeviceToHost, st));
-        OVL_CUDA_TRY(lat, cudaMemcpyAsync(&nit[i], P[i].iters, sizeof(int), cudaMemcpyDeviceToHost, st));
-    }
-    OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
+    for (int i = 0; i < nsolve; i++)
+        if (syl_on[i]) nit[i] += nit_extra[i];  // iterations on H_k plus those on T
 
     // ---- recombination ----
     std::vector<GemvDev> gd(nsolve);
@@ -875,19 +1045,25 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         std::vector<const float2*> ch, cl;
         std::vector<double2> extra;
         for (int cidx = 0; cidx < n; cidx++) {
-            if (cidx < p.m_q) {
+            if (f64) {
+                ch.push_back(cidx < p.m_q ? (const float2*)(p.d->S64 + N * cidx)
+                                          : (const float2*)((double2*)p.Vhi + N * (cidx - p.m_q)));
+                cl.push_back(nullptr);
+            } else if (cidx < p.m_q) {
                 ch.push_back(p.d->S_hi + N * cidx);
                 cl.push_back(p.d->S_lo + N * cidx);
             } else {
                 ch.push_back(p.Vhi + N * (cidx - p.m_q));
-                cl.push_back(df ? p.Vlo + N * (cidx - p.m_q) : nullptr);
+                cl.push_back(!df ? nullptr
+                             : lo16 ? (const float2*)((const char*)p.Vlo + (size_t)4 * N * (cidx - p.m_q))
+                                    : p.Vlo + N * (cidx - p.m_q));
             }
         }
         if (p.scheme == OVL_DEFL_LR) {
             // R sgn(Lambda) L^dag b  (Eq. 22, f = sgn on the diagonal)
             for (int t = 0; t < p.m_defl; t++) {
-                ch.push_back(p.d->S_hi + N * t);
-                cl.push_back(p.d->S_lo + N * t);
+                ch.push_back(f64 ? (const float2*)(p.d->S64 + N * t) : p.d->S_hi + N * t);
+                cl.push_back(f64 ? nullptr : p.d->S_lo + N * t);
                 double lre = p.d->T_host[2 * t];
                 double sg = lre > 0 ? 1.0 : (lre < 0 ? -1.0 : 0.0);
                 extra.push_back(make_double2(sg * c1[i][t].x, sg * c1[i][t].y));
@@ -904,13 +1080,16 @@ extern "C" int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params
         gd[i].g = p.gcomb;
         gd[i].y = p.w;
         gd[i].ncol = (int)ch.size();
+        gd[i].f64 = f64;
+        gd[i].lo16_from = lo16 ? p.m_q : 0;  // the Krylov columns; Schur and LR columns keep FP32 low planes
+        gd[i].lo16_to = lo16 ? n : 0;
         gmax = std::max(gmax, gd[i].ncol);
     }
     OVL_CUDA_TRY(lat, cudaMemcpyAsync(d_gd, gd.data(), nsolve * sizeof(GemvDev), cudaMemcpyHostToDevice, st));
     double gb = 0.0;
     for (int i = 0; i < nsolve; i++) gb += (double)gd[i].ncol * N * 16.0 + N * 16.0;
     ProfScope pg(lat, 7, gb, st);
-    if (int rc = ovl_gemv_df(lat, d_gd, nsolve, gmax, st)) return rc;
+    if (int rc = ovl_gemv_df(lat, d_gd, nsolve, gmax, st, f64)) return rc;
     pg.end(st);
     // ---- outputs ----
     bool ydev = ovl_is_device_ptr(y);

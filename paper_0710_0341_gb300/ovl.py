@@ -15,7 +15,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(_HERE, "libovl.so")
 
 OVL_OK, OVL_EINVAL, OVL_ENOMEM, OVL_ECUDA, OVL_ENOCONV, OVL_ETIMEOUT, OVL_ENOTSUP = range(7)
-OVL_PREC_FP64, OVL_PREC_MIXED, OVL_PREC_MIXED_R12, OVL_PREC_FP64_DFSTENCIL = 0, 1, 2, 3
+OVL_PREC_FP64, OVL_PREC_MIXED, OVL_PREC_MIXED_R12, OVL_PREC_FP64_DFSTENCIL, OVL_PREC_FP64_PLAIN = 0, 1, 2, 3, 4
+OVL_PREC_DF40 = 5
 OVL_DEFL_NONE, OVL_DEFL_SCHUR, OVL_DEFL_LR = 0, 1, 2
 OVL_VEC_F64, OVL_VEC_F32 = 0, 1
 OVL_LINKS_F64, OVL_LINKS_F32, OVL_LINKS_R12, OVL_LINKS_F64DF = 0, 1, 2, 3
@@ -30,7 +31,7 @@ class OvlError(RuntimeError):
 class ovl_sign_params(C.Structure):
     _fields_ = [("mu", C.c_double), ("m_w", C.c_double), ("k", C.c_int), ("prec", C.c_int),
                 ("newton_max_iter", C.c_int), ("newton_tol", C.c_double), ("newton_fp64", C.c_int),
-                ("adapt_every", C.c_int), ("k_max", C.c_int), ("tol", C.c_double)]
+                ("adapt_every", C.c_int), ("k_max", C.c_int), ("tol", C.c_double), ("schur_route", C.c_int)]
 
 
 class ovl_sign_info(C.Structure):
@@ -52,8 +53,12 @@ _SIGS = {
     "ovl_set_deflation": (C.c_int, [_P, C.c_double, C.c_double, C.c_int, C.c_int, _P, _P, _P, C.POINTER(_P)]),
     "ovl_deflation_setup": (C.c_int, [_P, C.c_double, C.c_double, C.c_int, C.c_int, C.c_double, C.c_int,
                                       C.POINTER(_P)]),
+    "ovl_deflation_setup_ex": (C.c_int, [_P, C.c_double, C.c_double, C.c_int, C.c_int, C.c_double, C.c_int,
+                                         C.c_int, C.POINTER(_P)]),
     "ovl_get_deflation": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), _P, _P, _P]),
     "ovl_destroy_deflation": (C.c_int, [_P]),
+    "ovl_deflation_save": (C.c_int, [_P, C.c_char_p]),
+    "ovl_deflation_load": (C.c_int, [_P, C.c_char_p, C.POINTER(_P)]),
     "ovl_deflation_stats": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "ovl_sign_apply": (C.c_int, [_P, C.c_int, C.POINTER(ovl_sign_params), C.POINTER(_P), _P, _P,
                                  C.POINTER(ovl_sign_info)]),
@@ -71,6 +76,8 @@ _SIGS = {
     "ovl_mlp_train": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_float, C.c_float, _P]),
     "ovl_mlp_last_error": (C.c_char_p, [_P]),
     "ovl_link_spread": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "ovl_autotune": (C.c_int, [_P, C.c_int, _P, C.c_int, C.POINTER(C.c_int)]),
+    "ovl_autotune_shape": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "ovl_wait_selftest": (C.c_int, [_P, C.c_longlong, C.POINTER(C.c_int)]),
     "ovl_ritz_values": (C.c_int, [_P, C.c_double, C.c_double, C.c_int, _P, _P]),
     "ovl_profile": (C.c_int, [_P, C.c_int, _P]),
@@ -182,6 +189,13 @@ def ovl_deflation_setup(h, mu, m_w, scheme, m, tol=1e-12, max_restarts=500):
     return d
 
 
+def ovl_deflation_setup_ex(h, mu, m_w, scheme, m, tol=1e-12, max_restarts=500, poly_degree=-1):
+    d = _P()
+    _check(lib().ovl_deflation_setup_ex(h, float(mu), float(m_w), int(scheme), int(m), float(tol),
+                                        int(max_restarts), int(poly_degree), C.byref(d)), h)
+    return d
+
+
 def ovl_get_deflation(d, S_or_R=None, T=None, L=None, h=None):
     sch, m = C.c_int(), C.c_int()
     _check(lib().ovl_get_deflation(d, C.byref(sch), C.byref(m), _ptr(S_or_R), _ptr(T), _ptr(L)), h)
@@ -192,6 +206,16 @@ def ovl_deflation_stats(d):
     r, m = C.c_int(), C.c_int()
     _check(lib().ovl_deflation_stats(d, C.byref(r), C.byref(m)))
     return r.value, m.value
+
+
+def ovl_deflation_save(d, path):
+    _check(lib().ovl_deflation_save(d, os.fsencode(path)))
+
+
+def ovl_deflation_load(h, path):
+    d = _P()
+    _check(lib().ovl_deflation_load(h, os.fsencode(path), C.byref(d)), h)
+    return d
 
 
 def ovl_destroy_deflation(d):
@@ -214,6 +238,7 @@ def ovl_sign_apply(h, params, defl, b, y, info=True):
         P[i].adapt_every = int(p.get("adapt_every", 0))
         P[i].k_max = int(p.get("k_max", 0))
         P[i].tol = float(p.get("tol", 0.0))
+        P[i].schur_route = int(p.get("schur_route", 0))
     D = (_P * n)(*[(d.value if isinstance(d, _P) else d) if d is not None else None for d in (defl or [None] * n)])
     I = (ovl_sign_info * n)()
     rc = lib().ovl_sign_apply(h, n, P, D, _ptr(b), _ptr(y), I)
@@ -243,6 +268,7 @@ def ovl_overlap_apply(h, params, defl, x, y, adjoint=False):
         P[i].adapt_every = int(p.get("adapt_every", 0))
         P[i].k_max = int(p.get("k_max", 0))
         P[i].tol = float(p.get("tol", 0.0))
+        P[i].schur_route = int(p.get("schur_route", 0))
     D = (_P * n)(*[(d.value if isinstance(d, _P) else d) if d is not None else None for d in (defl or [None] * n)])
     I = (ovl_sign_info * n)()
     rc = lib().ovl_overlap_apply(h, n, P, D, _ptr(x), _ptr(y), int(bool(adjoint)), I)
@@ -271,6 +297,22 @@ def ovl_launch_count(h):
 
 PROF_CLASSES = ["stencil", "gs_pass_a", "gs_reduce", "gs_small", "gs_pass_b", "newton", "projection",
                 "recombination"]
+
+
+def ovl_autotune(h, nrhs=1, max_report=256):
+    """Time the stencil's launch shapes and keep the fastest per (format,
+    links); returns the timed candidates as dicts."""
+    buf = (C.c_double * (7 * max_report))()
+    n = C.c_int()
+    _check(lib().ovl_autotune(h, int(nrhs), C.cast(buf, _P), int(max_report), C.byref(n)), h)
+    keys = ("fmt", "links", "tpb", "tx", "ty", "tz", "us")
+    return [dict(zip(keys, [int(buf[7 * i + j]) for j in range(6)] + [buf[7 * i + 6]])) for i in range(n.value)]
+
+
+def ovl_autotune_shape(h, fmt, links):
+    s = (C.c_int * 4)()
+    _check(lib().ovl_autotune_shape(h, int(fmt), int(links), s), h)
+    return tuple(s)
 
 
 def ovl_profile(h, enable):

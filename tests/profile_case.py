@@ -1,4 +1,7 @@
-"""One batch of the 8^4 sign-function workload, for kernel profiling.
+"""Small cases of the sign-function workloads, for kernel profiling under ncu
+(not a test module: pytest collects only test_*.py).
+
+Default: one batch of the 8^4 workload.
 
 Runs ovl_sign_apply once for 8 solves (mu in {0, 0.1, 0.3, 0.6} x Schur/LR,
 k = 400, m = 30, FP64 mode) with deflation data imported from a seeded
@@ -7,15 +10,24 @@ so the expensive eigensolver setup is skipped), inside an NVTX range
 "sign_batch". Used as the command under ncu, e.g.
 
     ncu --set full --clock-control none -k regex:k_gs_update -s 200 -c 1 \\
-        python -m paper_0710_0341_gb300.profile_case
+        python tests/profile_case.py
 
-``python -m paper_0710_0341_gb300.profile_case stencil r12`` instead applies the
-stencil alone (24^3x48, one right-hand side, 12-real links) five times.
+``python tests/profile_case.py stencil r12`` instead applies the stencil alone
+(24^3x48, one right-hand side, 12-real links) five times;
+``python tests/profile_case.py c3 [prec]`` runs one solve of the 16^3x32
+workload's shape at reduced depth (one point source, k = 120, m = 40 Schur
+vectors from a seeded orthonormal block; prec 0 = the 48-bit mode,
+4 = plain FP64, 2 = mixed with 12-real links).
 """
+import os
+import sys
+
 import numpy as np
 import torch
 
-from paper_0710_0341_gb300 import build, ovl, synth
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+from paper_0710_0341_gb300 import build, ovl, synth  # noqa: E402
 
 
 def main():
@@ -60,10 +72,32 @@ def stencil(fmt_name="r12", dims=(24, 24, 24, 48), reps=5):
     print("stencil case done", fmt_name, dims)
 
 
-if __name__ == "__main__":
-    import sys
+def config3(prec=0, k=120, m=40):
+    """One solve of the 16^3x32 workload's shape (point source at the origin,
+    mu = 0.2, m_w = -1.2) at depth k with m seeded orthonormal Schur vectors."""
+    build.build()
+    dims = (16, 16, 16, 32)
+    N = 12 * int(np.prod(dims))
+    h = ovl.ovl_create_lattice(dims)
+    ovl.ovl_set_links(h, torch.from_numpy(synth.random_su3_field(dims, 0.3, 0)).cuda())
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.standard_normal((N, m)) + 1j * rng.standard_normal((N, m)))
+    cols = np.ascontiguousarray(Q.T.reshape((m,) + synth.lattice_shape(dims) + (4, 3)))
+    T = np.diag(np.linspace(0.3, 0.4, m).astype(complex))
+    d = ovl.ovl_set_deflation(h, 0.2, -1.2, ovl.OVL_DEFL_SCHUR, m, cols, T.ravel(order="F").copy(), None)
+    b = torch.from_numpy(synth.point_source(dims, 0, 0)).cuda()
+    y = torch.zeros_like(b)
+    infos = ovl.ovl_sign_apply(h, [dict(mu=0.2, m_w=-1.2, k=k, prec=int(prec))], [d], b, y)
+    torch.cuda.synchronize()
+    ovl.ovl_destroy_deflation(d)
+    ovl.ovl_destroy_lattice(h)
+    print("config3 case done; newton iterations", [i["newton_iters"] for i in infos])
 
+
+if __name__ == "__main__":
     if len(sys.argv) > 1 and sys.argv[1] == "stencil":
         stencil(*(sys.argv[2:3] or ["r12"]))
+    elif len(sys.argv) > 1 and sys.argv[1] == "c3":
+        config3(*(sys.argv[2:3] or [0]))
     else:
         main()

@@ -79,7 +79,7 @@ def test_parameter_structs_match_the_header():
         py = [(n, {C.c_int: "int", C.c_double: "double"}[t]) for n, t in cls._fields_]
         assert hdr == py, (tag, hdr, py)
     # natural alignment of the C layout: the sizes a C compiler gives these structs
-    assert C.sizeof(ovl.ovl_sign_params) == 64 and C.sizeof(ovl.ovl_sign_info) == 40
+    assert C.sizeof(ovl.ovl_sign_params) == 72 and C.sizeof(ovl.ovl_sign_info) == 40
 
 
 def test_constants_match_the_header():

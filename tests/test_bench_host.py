@@ -58,31 +58,80 @@ class _Torch:
 
 
 class _Lib:
-    OVL_PREC_FP64, OVL_PREC_MIXED, OVL_PREC_MIXED_R12, OVL_PREC_FP64_DFSTENCIL = 0, 1, 2, 3
+    OVL_PREC_FP64, OVL_PREC_MIXED, OVL_PREC_MIXED_R12, OVL_PREC_FP64_DFSTENCIL, OVL_PREC_FP64_PLAIN = 0, 1, 2, 3, 4
+    OVL_PREC_DF40 = 5
 
     def __init__(self):
         self.calls = []
 
     def ovl_sign_apply(self, h, params, defl, b, y):
+        assert len(params) == len(defl) == len(b.a)
         self.calls.append([p["prec"] for p in params])
         y.a[:] = b.a
 
 
-def test_mixed_modes_times_both_modes_on_the_batch(monkeypatch):
-    errs = {1: [5e-8] * 8, 2: [7e-8] * 7 + [2e-7], 3: [2e-9] * 8}
+class _Tensor2(_Tensor):
+    def __getitem__(self, s):
+        return _Tensor2(self.a[s])
+
+    def contiguous(self):
+        return self
+
+
+def test_precision_arms_time_each_form_once_on_its_sources(monkeypatch):
     lib = _Lib()
-    monkeypatch.setattr(bench, "reference_sketch", lambda: {"0.0": {}})
-    monkeypatch.setattr(bench, "accuracy", lambda y, sk: errs[lib.calls[-1][0]])
-    bd = _Tensor(np.ones((8, 4), complex))
-    out = bench.mixed_modes(_Torch, lib, None, [None] * 8, bd, 3)
-    # one warm-up and three timed calls per mode, each over the 8-solve batch in one precision
-    assert [c[0] for c in lib.calls] == [1] * 4 + [2] * 4 + [3] * 4
-    assert all(len(set(c)) == 1 and len(c) == 8 for c in lib.calls)
-    a, b = out["fp32_basis_fp32_links"], out["fp32_basis_r12_links"]
-    assert abs(a["ms_per_step"] - 50.0 / 3) < 1e-9
-    assert abs(a["solves_per_s"] - 8 / (50.0 / 3 / 1e3)) < 1e-6
-    assert a["meets_1e-8"] is False and b["rel_err_est_per_solve"][-1] == 2e-7
-    assert out["fp64_basis_double_float_stencil"]["meets_1e-8"] is True
+    errs = {4: [1e-12, 2e-12], 5: [3e-10] * 12, 2: [6e-8] * 12, 1: [5e-8, None] + [7e-8] * 10}
+    monkeypatch.setattr(bench, "accuracy", lambda ys, sk, keys: errs[lib.calls[-1][0]][:len(keys)])
+    bd = _Tensor2(np.ones((12, 4), complex))
+    out = bench.precision_arms(_Torch, lib, None, None, bd, {}, [f"{i}" for i in range(12)])
+    # one call per form: the plain FP64 form on 2 sources, the mixed forms on all 12
+    assert [(c[0], len(c)) for c in lib.calls] == [(4, 2), (5, 12), (2, 12), (1, 12)]
+    assert out["df40_bf16_low_planes"]["meets_1e-8"] is True
+    p = out["plain_fp64"]
+    assert p["solves"] == 2 and abs(p["ms_per_step"] - 50.0) < 1e-9 and abs(p["solves_per_s"] - 40.0) < 1e-9
+    assert p["meets_1e-8"] is True
+    assert out["mixed_fp32_basis_r12_links"]["meets_1e-8"] is False
+    assert out["mixed_fp32_basis_fp32_links"]["rel_err_per_solve"][1] is None
+
+
+def test_depth_cost_fit_recovers_the_model():
+    a, c, m = 0.3, 2e-3, 40
+    T = lambda k: a * k + c * (m * k + k * (k + 1) / 2)  # noqa: E731
+    assert abs(bench.fit_depth_cost({6: T(6), 18: T(18)}, m, 600) - T(600)) < 1e-9 * T(600)
+    # negative fitted parts (timing noise) are clamped at zero
+    assert bench.fit_depth_cost({6: 1.0, 18: 1.0}, m, 600) >= 0.0
+
+
+def test_sketch_error_is_the_relative_error_in_expectation():
+    from paper_0710_0341_gb300 import synth
+
+    rng = np.random.default_rng(0)
+    n = 4000
+    y = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    e = 1e-3 * (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+    P = synth.probe_vectors(n, 256)
+    sk = P.conj() @ y
+    ref = {"probe_re": list(sk.real), "probe_im": list(sk.imag), "norm": float(np.linalg.norm(y))}
+    est = bench.sketch_error(y + e, ref, P)
+    true = np.linalg.norm(e) / np.linalg.norm(y)
+    assert 0.8 * true < est < 1.2 * true
+    assert bench.accuracy([y, y], {"a": ref, "_meta": {}}, ["a", "b"])[1] is None
+
+
+def test_roofline_uses_the_dominant_class_and_the_committed_traffic_ratio():
+    prof = {"stencil": {"launches": 10, "ms": 1.0, "bytes": 1e9}, "gs_pass_a": {"launches": 10, "ms": 3.0, "bytes": 1e10},
+            "gs_pass_b": {"launches": 10, "ms": 5.0, "bytes": 2e10}}
+    r = bench.roofline(prof, {"hbm_gbs": 8000.0}, {"gs_pass_b": 1.01})
+    assert r["kernel"] == "gs_pass_b"
+    assert abs(r["achieved"] - 2e9 / 0.5e-3 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 8000.0) < 1e-12
+    assert abs(r["traffic"] - 1.01 * 2e9) < 1e-3
+    assert bench.roofline(prof, None, {})["traffic"] is None
+
+
+def test_committed_profiles_give_the_pass_b_traffic_ratio():
+    r = bench.traffic_ratios()
+    assert 0.9 < r.get("gs_pass_b", 1.0) < 1.3
 
 
 class _Buf:
@@ -135,6 +184,13 @@ class _StencilLib:
         self.calls.append((self.lat[h], nrhs, fmt, links))
         self.launches += self.on
 
+    def ovl_autotune(self, h, nrhs):
+        self.tuned = getattr(self, "tuned", 0) + 1
+        return []
+
+    def ovl_autotune_shape(self, h, fmt, links):
+        return (128, 8, 4, 4)
+
     def ovl_profile(self, h, enable):
         self.on = bool(enable)
         if enable:
@@ -162,12 +218,15 @@ def test_stencil_cases_count_spinors_per_rhs_and_links_once():
         assert r["rhs"] == nrhs and r["bytes_per_site"] == bps
         assert abs(r["us_per_launch"] - 10.0) < 1e-9
         assert abs(r["GB_per_s"] - V * bps / 10e-6 / 1e9) < 1e-6 * r["GB_per_s"]
-    # 3 warm-up and 20 timed launches per case, the 12-rhs case in one launch each
-    assert len(lib.calls) == 5 * 23 and lib.calls[-1] == ((16, 16, 16, 32), 12, 1, 2)
+    # per case 3 warm-up and 20 timed launches with the built-in shape, then the
+    # same after the autotuner (once per lattice); the 12-rhs case in one launch each
+    assert len(lib.calls) == 2 * 5 * 23 and lib.calls[-1] == ((16, 16, 16, 32), 12, 1, 2)
+    assert lib.tuned == 3
+    assert all(res[k]["shape_tpb_tx_ty_tz"] == (128, 8, 4, 4) and "builtin_shape" in res[k] for k in expect)
     assert ((24, 24, 24, 48), 1, 0, 3) in lib.calls  # FP64 data, double-float links format
 
 
 def test_amortised_throughput_includes_the_setup():
     a = bench.amortised(100.0, 250.0, 8)
-    assert abs(a["1_sources_per_operator"] - 8 / 100.25) < 1e-12
-    assert abs(a["12_sources_per_operator"] - 96 / 103.0) < 1e-12
+    assert abs(a["1_batches_per_setup"] - 8 / 100.25) < 1e-12
+    assert abs(a["12_batches_per_setup"] - 96 / 103.0) < 1e-12

@@ -16,8 +16,11 @@ def _cols(X, m):
     return X.reshape(m, -1).T  # canonical spinors -> N x m
 
 
-@pytest.mark.parametrize("dims,m", [((2, 2, 2, 4), 12), ((4, 4, 4, 4), 20)])
-def test_setup_schur_and_lr_against_dense(dims, m):
+@pytest.mark.parametrize("dims,m,poly", [((2, 2, 2, 4), 12, -1), ((4, 4, 4, 4), 20, -1), ((4, 4, 4, 4), 20, 0),
+                                         ((4, 4, 4, 4), 20, 15)])
+def test_setup_schur_and_lr_against_dense(dims, m, poly):
+    """poly: -1 the Chebyshev filter with the automatic degree, 0 plain
+    restarted Arnoldi on A^2, 15 the filter with a fixed degree."""
     need_gpu()
     mu, m_w = 0.3, -1.0
     U = synth.random_su3_field(dims, 0.5, 0)
@@ -29,7 +32,7 @@ def test_setup_schur_and_lr_against_dense(dims, m):
         N = Ad.shape[0]
         shp = (m,) + synth.lattice_shape(dims) + (4, 3)
         # Schur
-        ds = ovl.ovl_deflation_setup(h, mu, m_w, ovl.OVL_DEFL_SCHUR, m, 1e-12, 500)
+        ds = ovl.ovl_deflation_setup_ex(h, mu, m_w, ovl.OVL_DEFL_SCHUR, m, 1e-12, 500, poly)
         S = np.zeros(shp, complex)
         T = np.zeros(m * m, complex)
         ovl.ovl_get_deflation(ds, S, T, None, h)
@@ -46,7 +49,7 @@ def test_setup_schur_and_lr_against_dense(dims, m):
         Qo, _ = np.linalg.qr(R_o[:, :m])
         assert np.linalg.norm(S - Qo @ (Qo.conj().T @ S)) < 1e-9
         # LR
-        dl = ovl.ovl_deflation_setup(h, mu, m_w, ovl.OVL_DEFL_LR, m, 1e-12, 500)
+        dl = ovl.ovl_deflation_setup_ex(h, mu, m_w, ovl.OVL_DEFL_LR, m, 1e-12, 500, poly)
         R = np.zeros(shp, complex)
         L = np.zeros(shp, complex)
         lam = np.zeros(m, complex)

@@ -42,7 +42,10 @@ def test_iteration_limits_return_status():
         assert e.value.code == ovl.OVL_ENOCONV
         assert e.value.infos[0]["status"] == ovl.OVL_ENOCONV
         with pytest.raises(ovl.OvlError) as e:
-            ovl.ovl_deflation_setup(h, 0.3, -1.0, ovl.OVL_DEFL_SCHUR, 12, 1e-14, 1)
+            ovl.ovl_deflation_setup(h, 0.3, -1.0, ovl.OVL_DEFL_SCHUR, 12, 1e-300, 1)
+        assert e.value.code == ovl.OVL_ENOCONV
+        with pytest.raises(ovl.OvlError) as e:  # the unfiltered iteration too
+            ovl.ovl_deflation_setup_ex(h, 0.3, -1.0, ovl.OVL_DEFL_SCHUR, 12, 1e-300, 1, 0)
         assert e.value.code == ovl.OVL_ENOCONV
         # the handle still works after both failures
         ovl.ovl_sign_apply(h, [dict(mu=0.3, m_w=-1.0, k=10)], [None], b, y)

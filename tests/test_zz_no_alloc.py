@@ -37,17 +37,40 @@ def test_noalloc_matches_apply_hw_twice(links, tol):
 def test_noalloc_rejects_oversize_and_host_buffers():
     torch = need_gpu()
     dims = (16, 16, 16, 16)  # 65536 sites x 192 B: 2 rhs in + out = 50 MB > 32 MiB
+    small = (2, 2, 2, 2)
     h = lattice(dims, synth.unit_gauge_field(dims))
+    h2 = lattice(small, synth.unit_gauge_field(small))
     try:
         x = torch.zeros((2,) + synth.lattice_shape(dims) + (4, 3), dtype=torch.complex128, device="cuda")
         with pytest.raises(ovl.OvlError) as e:
             ovl.ovl_apply_Hw_noalloc(h, 0.1, -1.0, x, torch.zeros_like(x), 2, ovl.OVL_LINKS_F64)
         assert e.value.code == ovl.OVL_EINVAL
-        xs = np.zeros((1,) + synth.lattice_shape((2, 2, 2, 2)) + (4, 3), complex)
-        h2 = lattice((2, 2, 2, 2), synth.unit_gauge_field((2, 2, 2, 2)))
+        xs = np.zeros((1,) + synth.lattice_shape(small) + (4, 3), complex)
         with pytest.raises(ovl.OvlError) as e:
             ovl.ovl_apply_Hw_noalloc(h2, 0.1, -1.0, xs, np.zeros_like(xs), 1, ovl.OVL_LINKS_F64)
         assert e.value.code == ovl.OVL_EINVAL
+    finally:
         ovl.ovl_destroy_lattice(h2)
+        ovl.ovl_destroy_lattice(h)
+
+
+def test_noalloc_calls_leave_free_device_memory_unchanged():
+    """On a fresh handle that never ran ovl_apply_Hw (which grows the handle's
+    own staging buffer): after one warm-up call, further calls change the
+    device's free memory by nothing."""
+    torch = need_gpu()
+    dims = (4, 4, 4, 6)
+    h = lattice(dims, synth.random_su3_field(dims, 0.5, 0))
+    try:
+        x = to_dev(torch, np.stack([synth.gaussian_source(dims, 5)] * 3))
+        out = torch.zeros_like(x)
+        torch.cuda.synchronize()
+        ovl.ovl_apply_Hw_noalloc(h, 0.2, -1.0, x, out, 3, ovl.OVL_LINKS_F64)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for links in (ovl.OVL_LINKS_F64, ovl.OVL_LINKS_R12, ovl.OVL_LINKS_F64):
+            ovl.ovl_apply_Hw_noalloc(h, 0.2, -1.0, x, out, 3, links)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
     finally:
         ovl.ovl_destroy_lattice(h)
