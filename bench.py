@@ -42,10 +42,13 @@ K_KRYLOV, M_DEFL, NSRC = 600, 40, 12
 METRIC = "sgn(H_w(mu)) b solves/s at 1e-8 rel err vs FP64 oracle"
 WORKLOAD = ("16^3x32 eps=0.3 m_w=-1.2 mu=0.2, 12 spin-colour point sources at the origin in one batched call, "
             "k=600, Schur m=40 (GPU setup)")
-DTYPE = "df48"
-DTYPE_DETAIL = ("FP64 stencil; Krylov basis as FP32 hi+lo pairs (48-bit); FP32 products in the orthogonality-"
-                "steering pass; double-float (48-bit) accumulation in the update pass, projections and "
-                "recombination; FP64 small-step scalars; double-float Newton")
+DTYPE_DETAIL = {
+    "df48": ("FP64 stencil; Krylov basis as FP32 hi+lo pairs (48-bit); FP32 products in the orthogonality-"
+             "steering pass; double-float (48-bit) accumulation in the update pass, projections and "
+             "recombination; FP64 small-step scalars; double-float Newton"),
+    "df40": ("as df48 with the Krylov columns' low parts stored as BF16 (FP32 hi + BF16 lo, about 32 "
+             "significant bits per entry, 12 bytes per complex entry); deflation vectors keep 48 bits"),
+}
 # the 8^4 batch of the Schur/LR comparison (reported as an extra)
 DIMS8, EPS8, MW8, MUS8, K8, M8 = (8, 8, 8, 8), 0.4, -1.0, [0.0, 0.1, 0.3, 0.6], 400, 30
 
@@ -293,6 +296,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline only (no precision arms, 8^4, stencil)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--prec", default="df48", choices=["df48", "df40"], help="arithmetic of the timed form")
     ap.add_argument("--defl-cache", default=None,
                     help="deflation data file: loaded when it exists (setup skipped), else written after the setup")
     args = ap.parse_args()
@@ -334,7 +338,8 @@ def main():
     tuned = {f"{f}/{l}": ovl.ovl_autotune_shape(h, f, l) for f, l in ((0, 0), (1, 1), (1, 2))}
     srcs = sources()
     b = np.stack([synth.point_source(DIMS, s, c) for s, c in srcs])
-    params = [dict(mu=MU, m_w=MW, k=K_KRYLOV, prec=ovl.OVL_PREC_FP64)] * NSRC
+    prec = {"df48": ovl.OVL_PREC_FP64, "df40": ovl.OVL_PREC_DF40}[args.prec]
+    params = [dict(mu=MU, m_w=MW, k=K_KRYLOV, prec=prec)] * NSRC
     defl = [d] * NSRC
     bd = torch.from_numpy(b).cuda()
     yd = torch.zeros_like(bd)
@@ -391,10 +396,15 @@ def main():
     extras = {}
     if rank == 0 and not args.no_extras:
         extras["precision_forms"] = guarded(lambda: precision_arms(torch, ovl, h, d, bd, sketch, keys))
+    ovl.ovl_destroy_deflation(d)
+    ovl.ovl_destroy_lattice(h)  # frees its 194 GB workspace before the other workloads
+    del bd, yd
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_extras:
         extras["stencil"] = guarded(lambda: stencil_gbs(torch, ovl, synth))
         extras["schur_lr_8x4"] = guarded(lambda: extra_8x4(torch, ovl, synth))
-    ovl.ovl_destroy_deflation(d)
-    ovl.ovl_destroy_lattice(h)
+        extras["uneven_batch_12x4"] = guarded(lambda: extra_12x4(torch, ovl, synth))
+        extras["small_4x4"] = guarded(lambda: extra_4x4(torch, ovl, synth))
     # ---- CPU oracle baseline (rank 0, N = 1) ----
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -406,7 +416,7 @@ def main():
         ok = [None if a is None else a < 1e-8 for a in acc]
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": DTYPE, "dtype_detail": DTYPE_DETAIL, "data": "synthetic",
+                "vs_baseline": None, "dtype": args.prec, "dtype_detail": DTYPE_DETAIL[args.prec], "data": "synthetic",
                 "config": {"workload": WORKLOAD, "solves_per_step": NSRC, "parallelism": f"replicas{ws}",
                            "l2": "working set 194 GB >> 129 MB L2, no flush"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
@@ -521,6 +531,88 @@ def extra_8x4(torch, ovl, synth):
         for x in adj + defl:
             ovl.ovl_destroy_deflation(x)
         return res
+    finally:
+        ovl.ovl_destroy_lattice(h)
+
+
+def extra_12x4(torch, ovl, synth, kmin=150, kmax=700, every=25):
+    """The uneven batch on 12^4 (eps 0.4, m_w -1): 12 spin-colour point
+    sources x mu in {0.05, 0.2, 0.4, 0.8} = 48 solves with Schur deflation
+    (m = 30, GPU setup per mu). Each solve's depth comes from the adaptive
+    estimate (tol 1e-8, checks every 25 steps from k = 150, at most 700);
+    the batch of those uneven depths is then timed with eager launches and
+    replayed from a CUDA graph."""
+    dims, mus, m = (12, 12, 12, 12), (0.05, 0.2, 0.4, 0.8), 30
+    h = ovl.ovl_create_lattice(dims, 0, None)
+    try:
+        ovl.ovl_set_links(h, torch.from_numpy(synth.random_su3_field(dims, 0.4, SEED)).cuda())
+        ovl.ovl_autotune(h, 48)
+        t0 = time.perf_counter()
+        dd = {mu: ovl.ovl_deflation_setup(h, mu, -1.0, ovl.OVL_DEFL_SCHUR, m, 1e-12, 1000) for mu in mus}
+        setup_s = time.perf_counter() - t0
+        srcs = sources()
+        b = np.stack([synth.point_source(dims, s, c) for s, c in srcs] * len(mus))
+        mu_of = [mu for mu in mus for _ in srcs]
+        defl = [dd[mu] for mu in mu_of]
+        bd = torch.from_numpy(b).cuda()
+        yd = torch.zeros_like(bd)
+        ad = [dict(mu=mu, m_w=-1.0, k=kmin, adapt_every=every, k_max=kmax, tol=1e-8) for mu in mu_of]
+        infos = ovl.ovl_sign_apply(h, ad, defl, bd, yd)
+        ks = [i["k_used"] for i in infos]
+        params = [dict(mu=mu, m_w=-1.0, k=k) for mu, k in zip(mu_of, ks)]
+        out = {"solves": len(params), "k_per_mu": {f"{mu}": sorted({k for k, x in zip(ks, mu_of) if x == mu})
+                                                     for mu in mus},
+               "adaptive_err_est_max": max(i["err_est"] for i in infos), "setup_s": setup_s}
+        for name, g in (("eager", 0), ("graph", 1)):
+            ovl.ovl_set_graphs(h, g)
+            for _ in range(2):  # the second call of a shape captures the graph
+                ovl.ovl_sign_apply(h, params, defl, bd, yd)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(2):
+                ovl.ovl_sign_apply(h, params, defl, bd, yd)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 2
+            out[name] = {"ms_per_batch": ms, "solves_per_s": len(params) / (ms / 1e3)}
+        out["graph_replays"] = ovl.ovl_set_graphs(h, -1)
+        ovl.ovl_set_graphs(h, 0)
+        for x in dd.values():
+            ovl.ovl_destroy_deflation(x)
+        return out
+    finally:
+        ovl.ovl_destroy_lattice(h)
+
+
+def extra_4x4(torch, ovl, synth, reps=20):
+    """The 4^4 workload (eps 0.5, m_w -1, mu 0.3, one complex Gaussian source,
+    k = 200, Schur m = 20 from the GPU setup), where launch latency rather
+    than bandwidth sets the time: one solve per call, eager launches against
+    the CUDA-graph replay of the Arnoldi loop."""
+    dims = (4, 4, 4, 4)
+    h = ovl.ovl_create_lattice(dims, 0, None)
+    try:
+        ovl.ovl_set_links(h, torch.from_numpy(synth.random_su3_field(dims, 0.5, SEED)).cuda())
+        d = ovl.ovl_deflation_setup(h, 0.3, -1.0, ovl.OVL_DEFL_SCHUR, 20, 1e-12, 1000)
+        bd = torch.from_numpy(synth.gaussian_source(dims, 1)).cuda()
+        yd = torch.zeros_like(bd)
+        p = [dict(mu=0.3, m_w=-1.0, k=200)]
+        out = {}
+        for name, g in (("eager", 0), ("graph", 1)):
+            ovl.ovl_set_graphs(h, g)
+            for _ in range(3):
+                ovl.ovl_sign_apply(h, p, [d], bd, yd)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            for _ in range(reps):
+                ovl.ovl_sign_apply(h, p, [d], bd, yd)
+            torch.cuda.synchronize()
+            out[name] = {"ms_per_solve": 1e3 * (time.perf_counter() - t) / reps}
+        ovl.ovl_set_graphs(h, 0)
+        ovl.ovl_destroy_deflation(d)
+        out["config"] = "4^4 eps=0.5 m_w=-1 mu=0.3, k=200, Schur m=20, one solve per call (wall time per call)"
+        return out
     finally:
         ovl.ovl_destroy_lattice(h)
 

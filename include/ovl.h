@@ -241,6 +241,16 @@ int ovl_deflation_load(ovl_lattice lat, const char* path, ovl_deflation* out);
 int ovl_sign_apply(ovl_lattice lat, int nsolve, const ovl_sign_params* params,
                    const ovl_deflation* defl, const double* b, double* y, ovl_sign_info* info);
 
+/* Device workspace (bytes, as a double) that ovl_sign_apply needs for this
+ * batch -- Krylov bases of k_max + 1 columns (k when not adaptive), the small
+ * matrices and the Newton work -- without running or allocating anything,
+ * so that a caller can size batches to the device memory it has (the
+ * predictor's admission, predictor.py). The lattice's workspace grows to the
+ * largest batch run on it and is kept until ovl_destroy_lattice. Errors as
+ * ovl_sign_apply's argument checks. */
+int ovl_sign_workspace_bytes(ovl_lattice lat, int nsolve, const ovl_sign_params* params,
+                             const ovl_deflation* defl, double* bytes);
+
 /* ---- the overlap operator (Sec. 1, Eq. 1) -------------------------------
  * adjoint = 0: y_i = D_ov(mu_i) x_i = x_i + gamma_5 sgn(H_w(mu_i)) x_i.
  * adjoint = 1: y_i = D_ov(mu_i)^dag x_i = x_i + sgn(H_w(-mu_i)) gamma_5 x_i
@@ -300,6 +310,17 @@ int ovl_ritz_values(ovl_lattice lat, double mu, double m_w, int k, const double*
  * 4 Gram-Schmidt pass B, 5 Newton sign, 6 FP64 projections, 7 recombination. */
 int ovl_launch_count(ovl_lattice lat, long long* n);
 int ovl_profile(ovl_lattice lat, int enable, double* stats);
+
+/* CUDA graphs for the Arnoldi loop of ovl_sign_apply (not in the paper).
+ * enable = 1: a fixed-depth batch (no adaptive depth, no ovl_profile timing)
+ * that repeats the shape of the previous call on this handle (same solves,
+ * depths, deflation data, mu values and workspace) is captured into a CUDA
+ * graph on its second call and replayed on every later one: one graph
+ * launch instead of five kernel launches per Arnoldi step. Results are
+ * those of the eager launches. A workspace that has to grow drops the graph.
+ * enable = 0: off (the default; drops the graph); -1: only query.
+ * replays (may be NULL): graph replays on this handle so far. */
+int ovl_set_graphs(ovl_lattice lat, int enable, long long* replays);
 
 /* Autotuner of the stencil's launch shape (not in the paper). For the FP32
  * stencil with 12-real and with 18-real links and the FP64 stencil, times

@@ -80,12 +80,20 @@ def critical_sparse(A, A_adj, m: int, nev: int | None = None, tol: float = 1e-13
     nev = nev or m + max(10, m // 4)
     lam, R, res = _critical_right_sparse(A, m, nev, tol)
     lamL, Lv, _ = _critical_right_sparse(A_adj, m, nev, tol)
+    return lam, R, pair_left(lam, R, lamL, Lv), res
+
+
+def pair_left(lam, R, lamL, Lv):
+    """Left vectors for the right eigenpairs (lam, R) from the right eigenpairs
+    (lamL, Lv) of A^dag: l_i is the vector with eigenvalue conj(lambda_i),
+    scaled so that l_i^dag r_i = 1 (Eq. 20)."""
+    m = len(lam)
     idx = [int(np.argmin(np.abs(lamL - np.conj(z)))) for z in lam]
     if len(set(idx)) != m:
         raise ValueError("left and right critical eigenvalues do not pair up")
     L = Lv[:, idx]
     d = np.einsum("ni,ni->i", L.conj(), R)
-    return lam, R, L / d.conj()[None, :], res
+    return L / d.conj()[None, :]
 
 
 def schur_from_right(A, R: np.ndarray):

@@ -13,7 +13,7 @@ namespace {
 
 using namespace ovl_stencil;
 
-template <typename T, typename VT, int LINKS>
+template <typename T, typename VT, int LINKS, bool TILED>
 __device__ __forceinline__ void dslash_site(const KArgs& a) {
     const int r = blockIdx.y;
     if (a.active && !a.active[(size_t)r * a.stride]) return;  // whole CTA (one right-hand side)
@@ -28,7 +28,7 @@ __device__ __forceinline__ void dslash_site(const KArgs& a) {
     }
     __syncthreads();
     size_t site;
-    if (a.tx) {  // tiled: block -> (tile x, y, z, t), thread -> site in the tile
+    if constexpr (TILED) {  // block -> (tile x, y, z, t), thread -> site in the tile
         unsigned b = blockIdx.x;
         const unsigned nbx = a.Lx / a.tx, nby = a.Ly / a.ty, nbz = a.Lz / a.tz;
         const unsigned bx = b % nbx;
@@ -48,16 +48,16 @@ __device__ __forceinline__ void dslash_site(const KArgs& a) {
 
 // FP64 spinors: the compiler's register choice (140 for FP64 links, 168 for the
 // double-float arithmetic on FP64 data; no spills)
-template <typename T, typename VT, int LINKS>
+template <typename T, typename VT, int LINKS, bool TILED = false>
 __global__ void __launch_bounds__(128) k_dslash(KArgs a) {
-    dslash_site<T, VT, LINKS>(a);
+    dslash_site<T, VT, LINKS, TILED>(a);
 }
 
 // FP32 spinors: at most 64 registers, 8 CTAs per SM (measured 13 % faster
 // than 96 registers with 12-real links at 24^3x48, in spite of a few spills)
-template <typename T, typename VT, int LINKS>
+template <typename T, typename VT, int LINKS, bool TILED = false>
 __global__ void __launch_bounds__(128, 8) k_dslash32(KArgs a) {
-    dslash_site<T, VT, LINKS>(a);
+    dslash_site<T, VT, LINKS, TILED>(a);
 }
 
 }  // namespace
@@ -98,19 +98,32 @@ int ovl_dslash_launch(ovl_lattice lat, const DslashArgs& d, int fmt, int links, 
         const int tpb = sh.tx ? tpb32 : sh.tpb ? sh.tpb
                                                : (lat->V * (size_t)d.nrhs < (size_t)1024 * lat->num_sms ? 32 : 128);
         dim3 g64(sh.tx ? ntile : (unsigned)((lat->V + tpb - 1) / tpb), (unsigned)d.nrhs);
-        if (links == OVL_LINKS_F64DF)  // same shapes as FP64 (at 8^4 x 8 rhs: 81 us with 32 or 128 threads)
-            k_dslash<dd, double2, OVL_LINKS_F64><<<g64, tpb, 0, st>>>(a);
-        else if (links == OVL_LINKS_F64)
-            k_dslash<double, double2, OVL_LINKS_F64><<<g64, tpb, 0, st>>>(a);
-        else if (links == OVL_LINKS_F32)
+        const bool t = sh.tx != 0;  // tiled variants are separate instantiations (no extra registers otherwise)
+        if (links == OVL_LINKS_F64DF) {  // same shapes as FP64 (at 8^4 x 8 rhs: 81 us with 32 or 128 threads)
+            if (t)
+                k_dslash<dd, double2, OVL_LINKS_F64, true><<<g64, tpb, 0, st>>>(a);
+            else
+                k_dslash<dd, double2, OVL_LINKS_F64><<<g64, tpb, 0, st>>>(a);
+        } else if (links == OVL_LINKS_F64) {
+            if (t)
+                k_dslash<double, double2, OVL_LINKS_F64, true><<<g64, tpb, 0, st>>>(a);
+            else
+                k_dslash<double, double2, OVL_LINKS_F64><<<g64, tpb, 0, st>>>(a);
+        } else if (links == OVL_LINKS_F32) {
             k_dslash<float, double2, OVL_LINKS_F32><<<g64, tpb, 0, st>>>(a);
-        else
+        } else {
             k_dslash<float, double2, OVL_LINKS_R12><<<g64, tpb, 0, st>>>(a);
+        }
     } else {
+        const bool t = sh.tx != 0;
         if (links == OVL_LINKS_F64 || links == OVL_LINKS_F64DF)
             return ovl_fail(lat, OVL_ENOTSUP, "F32 spinors with F64 links are not built");
+        else if (links == OVL_LINKS_F32 && t)
+            k_dslash32<float, float2, OVL_LINKS_F32, true><<<grid, tpb32, 0, st>>>(a);
         else if (links == OVL_LINKS_F32)
             k_dslash32<float, float2, OVL_LINKS_F32><<<grid, tpb32, 0, st>>>(a);
+        else if (t)
+            k_dslash32<float, float2, OVL_LINKS_R12, true><<<grid, tpb32, 0, st>>>(a);
         else
             k_dslash32<float, float2, OVL_LINKS_R12><<<grid, tpb32, 0, st>>>(a);
     }

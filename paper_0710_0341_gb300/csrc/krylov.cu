@@ -16,6 +16,8 @@
 // pass-B arithmetic for whatever coefficients are used, so the inner products
 // of pass A only need FP32 products (they steer orthogonality), while pass B
 // accumulates in double-float (48 bits) against the stored hi+lo basis.
+#include <stdlib.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -536,8 +538,8 @@ __global__ void __launch_bounds__(SR_THREADS) k_gs_small_rows(BatchDev B, int j)
 // ---------------------------------------------------------------------------
 // pass B: q_{p+1} and u_{j+1} (see the file header)
 // ---------------------------------------------------------------------------
-template <int LO>  // 0: no low plane; 1: FP32 low planes; 2: BF16 low planes of the Krylov columns
-__global__ void __launch_bounds__(256, 3) k_gs_update(BatchDev B, int j) {
+template <int LO, int MINB = 3>  // LO 0: no low plane; 1: FP32 low planes; 2: BF16 low planes of the Krylov columns
+__global__ void __launch_bounds__(256, MINB) k_gs_update(BatchDev B, int j) {
     constexpr bool DF = LO > 0;
     const int s = blockIdx.y;
     const SolveDev& d = B.sd[s];
@@ -580,7 +582,45 @@ __global__ void __launch_bounds__(256, 3) k_gs_update(BatchDev B, int j) {
         }
         // columns in descending order (pass A read them ascending: the most
         // recently read ones may still be in L2); two columns per iteration
-        for (int c0 = p - 1 - warp; c0 >= 0; c0 -= 16) {
+        int c0 = p - 1 - warp;
+        if constexpr (LO == 2) {
+            // Krylov columns (c >= nptr): FP32 high plane + BF16 low plane, no
+            // per-column branches so that all four loads of a lane are in flight
+            const __nv_bfloat162* __restrict__ vlo16 = (const __nv_bfloat162*)d.vlo;
+            for (; c0 - 8 >= nptr; c0 -= 16) {
+                float4 h4[2][UPD_RPL / 2], l4[2][UPD_RPL / 2];
+#pragma unroll
+                for (int bb = 0; bb < 2; bb++) {
+                    const size_t off = (size_t)(c0 - 8 * bb - nptr) * N;
+                    const float4* __restrict__ qh = (const float4*)(d.vhi + off);
+                    const void* ql16 = (const void*)(vlo16 + off);
+#pragma unroll
+                    for (int i = 0; i < UPD_RPL / 2; i++) {
+                        const size_t r = base + 64 * i + 2 * lane;
+                        const bool ok = full || r < N;
+                        h4[bb][i] = ok ? __ldg(qh + (r >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        l4[bb][i] = ok ? lo16_pair(ql16, r >> 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+#pragma unroll
+                for (int bb = 0; bb < 2; bb++) {
+                    const int c = c0 - 8 * bb;
+                    const float2 apc = s_ap[c], ghc = s_gh[c], glc = s_gl[c];
+#pragma unroll
+                    for (int i = 0; i < UPD_RPL / 2; i++) {
+                        const float4 hv = h4[bb][i], lv = l4[bb][i];
+                        const float2 h0 = make_float2(hv.x, hv.y), h1 = make_float2(hv.z, hv.w);
+                        sq[2 * i].x = fmaf(h0.x, apc.x, fmaf(-h0.y, apc.y, sq[2 * i].x));
+                        sq[2 * i].y = fmaf(h0.x, apc.y, fmaf(h0.y, apc.x, sq[2 * i].y));
+                        sq[2 * i + 1].x = fmaf(h1.x, apc.x, fmaf(-h1.y, apc.y, sq[2 * i + 1].x));
+                        sq[2 * i + 1].y = fmaf(h1.x, apc.y, fmaf(h1.y, apc.x, sq[2 * i + 1].y));
+                        dfacc_mac(sg[2 * i], h0, make_float2(lv.x, lv.y), ghc, glc);
+                        dfacc_mac(sg[2 * i + 1], h1, make_float2(lv.z, lv.w), ghc, glc);
+                    }
+                }
+            }
+        }
+        for (; c0 >= 0; c0 -= 16) {
             float4 h4[2][UPD_RPL / 2], l4[2][UPD_RPL / 2];
 #pragma unroll
             for (int bb = 0; bb < 2; bb++) {
@@ -1183,6 +1223,8 @@ int ovl_gs_update(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
                                                64 * 1024));
         OVL_CUDA_TRY(lat, cudaFuncSetAttribute(k_gs_update<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                64 * 1024));
+        OVL_CUDA_TRY(lat, cudaFuncSetAttribute(k_gs_update<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               64 * 1024));
         lat->gs_update_attr = true;
     }
     if (b.f64) {
@@ -1191,8 +1233,13 @@ int ovl_gs_update(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
             OVL_CUDA_TRY(lat, cudaFuncSetAttribute(k_gs_update64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)dyn64));
         k_gs_update64<<<grid, 256, dyn64, st>>>(b, j);
-    } else if (b.lo16)
-        k_gs_update<2><<<grid, 256, dyn, st>>>(b, j);
+    } else if (b.lo16) {
+        static const int minb = getenv("OVL_PASSB_MINB") ? atoi(getenv("OVL_PASSB_MINB")) : 3;
+        if (minb == 2)
+            k_gs_update<2, 2><<<grid, 256, dyn, st>>>(b, j);
+        else
+            k_gs_update<2><<<grid, 256, dyn, st>>>(b, j);
+    }
     else if (b.df)
         k_gs_update<1><<<grid, 256, dyn, st>>>(b, j);
     else

@@ -100,6 +100,7 @@ static void free_links(LinkSet& s) {
 extern "C" int ovl_destroy_lattice(ovl_lattice lat) {
     if (!lat) return OVL_OK;
     cudaStreamSynchronize(lat->stream);
+    if (lat->graph_exec) cudaGraphExecDestroy(lat->graph_exec);
     free_links(lat->links);
     ovl_prof_flush(lat);
     for (cudaEvent_t e : lat->event_pool) cudaEventDestroy(e);

@@ -69,6 +69,11 @@ struct ovl_lattice_s {
     bool gs_update_attr = false;   // pass B may take more than 48 KB of shared memory
     // stencil launch shapes per [spinor format F64/F32][link type], set by ovl_autotune
     OvlStenShape sten_shape[2][4];
+    // CUDA graph of the fixed-depth Arnoldi loop of ovl_sign_apply (ovl_set_graphs)
+    bool graphs = false;
+    cudaGraphExec_t graph_exec = nullptr;
+    uint64_t graph_key = 0, graph_seen = 0;
+    long long graph_kernels = 0, graph_replays = 0;
     // kernels launched by this handle, and optional per-class event timing
     long long launches = 0;
     bool prof = false;

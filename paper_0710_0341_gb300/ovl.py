@@ -62,6 +62,8 @@ _SIGS = {
     "ovl_deflation_stats": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "ovl_sign_apply": (C.c_int, [_P, C.c_int, C.POINTER(ovl_sign_params), C.POINTER(_P), _P, _P,
                                  C.POINTER(ovl_sign_info)]),
+    "ovl_sign_workspace_bytes": (C.c_int, [_P, C.c_int, C.POINTER(ovl_sign_params), C.POINTER(_P),
+                                           C.POINTER(C.c_double)]),
     "ovl_overlap_apply": (C.c_int, [_P, C.c_int, C.POINTER(ovl_sign_params), C.POINTER(_P), _P, _P, C.c_int,
                                     C.POINTER(ovl_sign_info)]),
     "ovl_deflation_adjoint": (C.c_int, [_P, C.POINTER(_P)]),
@@ -76,6 +78,7 @@ _SIGS = {
     "ovl_mlp_train": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_float, C.c_float, _P]),
     "ovl_mlp_last_error": (C.c_char_p, [_P]),
     "ovl_link_spread": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "ovl_set_graphs": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong)]),
     "ovl_autotune": (C.c_int, [_P, C.c_int, _P, C.c_int, C.POINTER(C.c_int)]),
     "ovl_autotune_shape": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "ovl_wait_selftest": (C.c_int, [_P, C.c_longlong, C.POINTER(C.c_int)]),
@@ -252,6 +255,33 @@ def ovl_sign_apply(h, params, defl, b, y, info=True):
     return infos
 
 
+def _params(params):
+    n = len(params)
+    P = (ovl_sign_params * n)()
+    for i, p in enumerate(params):
+        P[i].mu = p["mu"]
+        P[i].m_w = p["m_w"]
+        P[i].k = int(p["k"])
+        P[i].prec = int(p.get("prec", OVL_PREC_FP64))
+        P[i].newton_max_iter = int(p.get("newton_max_iter", 0))
+        P[i].newton_tol = float(p.get("newton_tol", 0.0))
+        P[i].newton_fp64 = int(p.get("newton_fp64", 0))
+        P[i].adapt_every = int(p.get("adapt_every", 0))
+        P[i].k_max = int(p.get("k_max", 0))
+        P[i].tol = float(p.get("tol", 0.0))
+        P[i].schur_route = int(p.get("schur_route", 0))
+    return P
+
+
+def ovl_sign_workspace_bytes(h, params, defl=None):
+    """Device bytes ovl_sign_apply needs for this batch (nothing runs)."""
+    n = len(params)
+    D = (_P * n)(*[(d.value if isinstance(d, _P) else d) if d is not None else None for d in (defl or [None] * n)])
+    out = C.c_double()
+    _check(lib().ovl_sign_workspace_bytes(h, n, _params(params), D, C.byref(out)), h)
+    return int(out.value)
+
+
 def ovl_overlap_apply(h, params, defl, x, y, adjoint=False):
     """D_ov(mu) x (adjoint=False) or D_ov(mu)^dag x (True) per solve; params and
     defl as in ovl_sign_apply (for the adjoint: deflation data of H_w(-mu))."""
@@ -297,6 +327,13 @@ def ovl_launch_count(h):
 
 PROF_CLASSES = ["stencil", "gs_pass_a", "gs_reduce", "gs_small", "gs_pass_b", "newton", "projection",
                 "recombination"]
+
+
+def ovl_set_graphs(h, enable):
+    """enable 1/0 CUDA-graph replay of the Arnoldi loop, -1 query; returns the replay count."""
+    n = C.c_longlong()
+    _check(lib().ovl_set_graphs(h, int(enable), C.byref(n)), h)
+    return n.value
 
 
 def ovl_autotune(h, nrhs=1, max_report=256):

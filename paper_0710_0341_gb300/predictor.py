@@ -161,6 +161,39 @@ def nearest_m(m):
     return min(M_GRID, key=lambda g: abs(g - m))
 
 
+def plan_depths(k_pred, margin=1.25, k_floor=20, every=10, k_cap=700):
+    """Adaptive depth settings from predicted depths: each solve starts its
+    checks at the predicted k (rounded down to the check interval) and may run
+    to margin x k (the adaptive estimate is the fallback when the prediction is
+    short); the basis is sized for that k_max."""
+    out = []
+    for k in np.atleast_1d(k_pred):
+        k0 = min(k_cap, max(k_floor, int(k) // every * every))
+        out.append((k0, max(k0, min(k_cap, int(math.ceil(margin * k))))))
+    return out
+
+
+def admit(h, params, defl, budget_bytes, workspace=None):
+    """Split the solves into batches whose device workspace (the library's
+    ovl_sign_workspace_bytes for the batch) fits budget_bytes. Solves are
+    taken by decreasing basis size (k_max, else k) and each goes to the first
+    batch it fits in; a solve that does not fit alone raises ValueError.
+    Returns lists of solve indices."""
+    ws = workspace or (lambda p, d: ovl.ovl_sign_workspace_bytes(h, p, d))
+    order = sorted(range(len(params)), key=lambda i: -max(params[i]["k"], params[i].get("k_max", 0)))
+    batches = []
+    for i in order:
+        if ws([params[i]], [defl[i]]) > budget_bytes:
+            raise ValueError(f"solve {i} needs more than {budget_bytes} bytes on its own")
+        for bt in batches:
+            if ws([params[j] for j in bt + [i]], [defl[j] for j in bt + [i]]) <= budget_bytes:
+                bt.append(i)
+                break
+        else:
+            batches.append([i])
+    return [sorted(bt) for bt in batches]
+
+
 if __name__ == "__main__":
     import sys
 

@@ -23,6 +23,7 @@ import pytest
 
 import oracle_jobs
 from helpers import canon_cols, lattice, need_gpu, rel
+from oracle import eigen
 from paper_0710_0341_gb300 import ovl, synth
 
 pytestmark = [pytest.mark.gpu, pytest.mark.late]
@@ -30,6 +31,9 @@ pytestmark = [pytest.mark.gpu, pytest.mark.late]
 DIMS8, EPS8, MW = (8, 8, 8, 8), 0.4, -1.0
 K8, M8 = 400, 30
 DIMS12, EPS12, K12 = (12, 12, 12, 12), 0.4, 300
+
+
+MUS12, KS12 = (0.05, 0.2, 0.4, 0.8), (150, 170, 190, 210)
 
 
 @pytest.fixture(scope="module")
@@ -40,69 +44,67 @@ def oracle_pool():
     for v in keep:
         os.environ[v] = "4"
     ex = cf.ProcessPoolExecutor(max_workers=4, mp_context=mp.get_context("spawn"))
-    jobs = {
-        0.0: ex.submit(oracle_jobs.deflated_case, DIMS8, EPS8, MW, 0.0, M8, K8, ("schur", "lr")),
-        0.3: ex.submit(oracle_jobs.deflated_case, DIMS8, EPS8, MW, 0.3, M8, K8, ("schur",)),
-        0.6: ex.submit(oracle_jobs.deflated_case, DIMS8, EPS8, MW, 0.6, M8, K8, ("lr",)),
-        "12x4": ex.submit(oracle_jobs.undeflated_case, DIMS12, EPS12, MW, 0.0, K12),
-    }
+    jobs = {("pairs", mu): ex.submit(oracle_jobs.right_pairs, DIMS8, EPS8, MW, mu, M8) for mu in (0.0, 0.3, 0.6, -0.6)}
+    jobs["12x4"] = ex.submit(oracle_jobs.undeflated_case, DIMS12, EPS12, MW, 0.0, K12)
+    for mu, k in zip(MUS12, KS12):
+        jobs[("12x4", mu)] = ex.submit(oracle_jobs.undeflated_case, DIMS12, EPS12, MW, mu, k)
     for v, x in keep.items():
         if x is None:
             os.environ.pop(v, None)
         else:
             os.environ[v] = x
-    yield jobs
+    yield ex, jobs
     ex.shutdown(wait=True, cancel_futures=True)
 
 
-def _schur(h, mu, r):
-    return ovl.ovl_set_deflation(h, mu, MW, ovl.OVL_DEFL_SCHUR, M8, canon_cols(r["S"], DIMS8),
-                                 np.asfortranarray(r["T"]).ravel(order="F").copy(), None)
-
-
-def _lr(h, mu, r):
-    return ovl.ovl_set_deflation(h, mu, MW, ovl.OVL_DEFL_LR, M8, canon_cols(r["R"], DIMS8),
-                                 np.ascontiguousarray(r["lam"]), canon_cols(r["L"], DIMS8))
+def _deflated_oracle(pool):
+    """Critical pairs (right; left of mu = 0.6 from H_w(-0.6)) and the oracle's
+    results of the four cases, the solves submitted as their pairs arrive."""
+    ex, jobs = pool
+    pr = {mu: jobs[("pairs", mu)].result(timeout=1500) for mu in (0.0, 0.3, 0.6, -0.6)}
+    for r in pr.values():
+        assert r["res"] < 1e-8, r["res"]  # the imported vectors are eigenvectors to high accuracy
+    lam0, R0 = pr[0.0]["lam"], pr[0.0]["R"]
+    L0 = R0 / np.einsum("ni,ni->i", R0.conj(), R0).conj()[None, :]  # H_w(0) is Hermitian: L = R (Eq. 20)
+    L6 = eigen.pair_left(pr[0.6]["lam"], pr[0.6]["R"], pr[-0.6]["lam"], pr[-0.6]["R"])
+    data = {(0.0, "schur"): (lam0, R0, None), (0.0, "lr"): (lam0, R0, L0),
+            (0.3, "schur"): (pr[0.3]["lam"], pr[0.3]["R"], None), (0.6, "lr"): (pr[0.6]["lam"], pr[0.6]["R"], L6)}
+    futs = {c: ex.submit(oracle_jobs.deflated_solve, DIMS8, EPS8, MW, c[0], K8, c[1], *v) for c, v in data.items()}
+    return data, {c: f.result(timeout=1500) for c, f in futs.items()}
 
 
 def test_bench_shape_8x4_schur_and_lr_against_oracle(oracle_pool):
     """Schur at mu = 0 and 0.3, LR at mu = 0 and 0.6 in one batched call
-    (k = 400, m = 30, FP64 mode, default Newton): every solve within 1e-10 of
-    the oracle's same algorithm."""
+    (k = 400, m = 30, default Newton): the 48-bit mode and the plain FP64 form
+    within 1e-10 of the oracle's same algorithm, the 40-bit basis within 1e-8."""
     need_gpu()
     U = synth.random_su3_field(DIMS8, EPS8, 0)
     b = synth.gaussian_source(DIMS8, 1)
-    res = {mu: oracle_pool[mu].result(timeout=1500) for mu in (0.0, 0.3, 0.6)}
-    for r in res.values():
-        assert r["res"] < 1e-8, r["res"]  # the imported vectors are eigenvectors to high accuracy
+    data, ref = _deflated_oracle(oracle_pool)
     h = lattice(DIMS8, U)
     try:
         cases = [(0.0, "schur"), (0.0, "lr"), (0.3, "schur"), (0.6, "lr")]
-        defl = [_schur(h, mu, res[mu]) if s == "schur" else _lr(h, mu, res[mu]) for mu, s in cases]
+        defl = []
+        for c in cases:
+            lam, R, L = data[c]
+            if c[1] == "schur":
+                defl.append(ovl.ovl_set_deflation(h, c[0], MW, ovl.OVL_DEFL_SCHUR, M8, canon_cols(ref[c]["S"], DIMS8),
+                                                  np.asfortranarray(ref[c]["T"]).ravel(order="F").copy(), None))
+            else:
+                defl.append(ovl.ovl_set_deflation(h, c[0], MW, ovl.OVL_DEFL_LR, M8, canon_cols(R, DIMS8),
+                                                  np.ascontiguousarray(lam), canon_cols(L, DIMS8)))
         params = [dict(mu=mu, m_w=MW, k=K8) for mu, _ in cases]
-        y = np.zeros((len(cases),) + b.shape, complex)
-        infos = ovl.ovl_sign_apply(h, params, defl, np.stack([b] * len(cases)), y)
-        for i, (mu, s) in enumerate(cases):
-            assert infos[i]["status"] == 0 and infos[i]["k_used"] == K8 and infos[i]["m_used"] == M8
-            e = rel(y[i], res[mu][s])
-            print(f"8^4 {s} mu={mu}: FP64 mode rel err vs oracle {e:.3e}, Newton iterations {infos[i]['newton_iters']}")
-            assert e < 1e-10, (mu, s, e)
-        # the plain FP64 form (complex128 basis, FP64 Newton) on the same batch
-        y64 = np.zeros_like(y)
-        params64 = [dict(p, prec=ovl.OVL_PREC_FP64_PLAIN) for p in params]
-        ovl.ovl_sign_apply(h, params64, defl, np.stack([b] * len(cases)), y64)
-        for i, (mu, s) in enumerate(cases):
-            e = rel(y64[i], res[mu][s])
-            print(f"8^4 {s} mu={mu}: plain FP64 rel err vs oracle {e:.3e}")
-            assert e < 1e-10, ("plain fp64", mu, s, e)
-        # the 40-bit basis (BF16 low planes) on the same batch: within 1e-8
-        y40 = np.zeros_like(y)
-        ovl.ovl_sign_apply(h, [dict(p, prec=ovl.OVL_PREC_DF40) for p in params], defl,
-                           np.stack([b] * len(cases)), y40)
-        for i, (mu, s) in enumerate(cases):
-            e = rel(y40[i], res[mu][s])
-            print(f"8^4 {s} mu={mu}: df40 rel err vs oracle {e:.3e}")
-            assert e < 1e-8, ("df40", mu, s, e)
+        bb = np.stack([b] * len(cases))
+        for prec, name, bar in ((ovl.OVL_PREC_FP64, "48-bit mode", 1e-10), (ovl.OVL_PREC_FP64_PLAIN, "plain FP64", 1e-10),
+                                (ovl.OVL_PREC_DF40, "40-bit basis", 1e-8)):
+            y = np.zeros_like(bb)
+            infos = ovl.ovl_sign_apply(h, [dict(p, prec=prec) for p in params], defl, bb, y)
+            for i, c in enumerate(cases):
+                assert infos[i]["status"] == 0 and infos[i]["k_used"] == K8 and infos[i]["m_used"] == M8
+                e = rel(y[i], ref[c]["y"])
+                print(f"8^4 {c[1]} mu={c[0]}: {name} rel err vs oracle {e:.3e}, Newton iterations "
+                      f"{infos[i]['newton_iters']}")
+                assert e < bar, (name, c, e)
         for d in defl:
             ovl.ovl_destroy_deflation(d)
     finally:
@@ -126,7 +128,7 @@ def test_12x4_undeflated_k300_against_oracle(oracle_pool):
             info = ovl.ovl_sign_apply(h, [dict(mu=0.0, m_w=MW, k=K12, prec=prec)], [None], b, y)
             assert info[0]["k_used"] == K12
             ys[prec] = y
-        r = oracle_pool["12x4"].result(timeout=1500)
+        r = oracle_pool[1]["12x4"].result(timeout=1500)
         bb = np.vdot(b.ravel(), b.ravel()).real
         for prec, y in ys.items():
             e = rel(y, r["y"])
@@ -135,5 +137,35 @@ def test_12x4_undeflated_k300_against_oracle(oracle_pool):
                   f"(oracle {r['im_ratio']:.3e})")
             assert e < 1e-10, (prec, e)
             assert abs(im) <= abs(r["im_ratio"]) + 1e-12, (prec, im, r["im_ratio"])
+    finally:
+        ovl.ovl_destroy_lattice(h)
+
+
+def test_12x4_uneven_batch_one_solve_per_mu_against_oracle(oracle_pool):
+    """The 12^4 batch shape of the uneven-depth workload: one solve for each
+    mu in {0.05, 0.2, 0.4, 0.8} with depths 150, 170, 190, 210 in one call,
+    eager and replayed from a CUDA graph: every solve within 1e-10 of the
+    oracle (Eq. 11), the replay bit for bit equal to the eager launches."""
+    need_gpu()
+    U = synth.random_su3_field(DIMS12, EPS12, 0)
+    b = synth.gaussian_source(DIMS12, 1)
+    h = lattice(DIMS12, U)
+    try:
+        params = [dict(mu=mu, m_w=MW, k=k) for mu, k in zip(MUS12, KS12)]
+        bb = np.stack([b] * 4)
+        y = np.zeros_like(bb)
+        infos = ovl.ovl_sign_apply(h, params, [None] * 4, bb, y)
+        assert [i["k_used"] for i in infos] == list(KS12)
+        for i, mu in enumerate(MUS12):
+            r = oracle_pool[1][("12x4", mu)].result(timeout=1500)
+            e = rel(y[i], r["y"])
+            print(f"12^4 mu={mu} k={KS12[i]}: rel err vs oracle {e:.3e}")
+            assert e < 1e-10, (mu, e)
+        ovl.ovl_set_graphs(h, 1)
+        for _ in range(3):
+            yg = np.zeros_like(bb)
+            ovl.ovl_sign_apply(h, params, [None] * 4, bb, yg)
+            assert np.array_equal(yg, y)
+        assert ovl.ovl_set_graphs(h, -1) >= 1
     finally:
         ovl.ovl_destroy_lattice(h)

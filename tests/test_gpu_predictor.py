@@ -55,3 +55,56 @@ def test_predictor_beats_the_method_without_it():
     # the depth estimate sizes the basis: rarely far below the depth needed
     k_true = np.exp(Tt[:, 0])
     assert np.mean(k_hat >= 0.7 * k_true) >= 0.75
+
+
+def test_predicted_depths_size_and_admit_batches():
+    """The predictor in its role: for held-out configurations (undeflated,
+    as the predictor's m = 0 option) the predicted depth starts the adaptive
+    checks and sizes the basis (k_max = 1.25 k_hat), and the solves are split
+    by predictor.admit into batches that fit a device budget of half the
+    workspace of the whole set; each batch's results equal the same solves run
+    in one call, and every solve that stopped before its k_max reached the
+    estimate's 1e-8 target."""
+    torch = need_gpu()
+    from paper_0710_0341_gb300 import ovl, synth
+
+    if not os.path.exists(predictor.DATA):
+        pytest.skip("no predictor training data")
+    rows = [r for r in json.load(open(predictor.DATA))["rows"] if r["label"] is not None]
+    n_tr = (3 * len(rows)) // 4
+    X, T = predictor.to_xy(rows[:n_tr])
+    p = predictor.Predictor(seed=0)
+    try:
+        p.fit(X, T, steps=3000, lr=3e-3)
+        test = rows[n_tr:n_tr + 6]
+        k_hat, _ = p.predict(np.array([r["features"] for r in test], dtype=np.float32))
+    finally:
+        p.close()
+    dims = tuple(json.load(open(predictor.DATA))["dims"])
+    plans = predictor.plan_depths(k_hat)
+    for r, (k0, km) in zip(test, plans):  # one lattice per configuration: the same links only within a row
+        cfg = r["config"]
+        h = ovl.ovl_create_lattice(dims)
+        try:
+            ovl.ovl_set_links(h, synth.random_su3_field(dims, cfg["eps"], cfg["seed"]))
+            b = synth.gaussian_source(dims, cfg["seed"] + 1)
+            params = [dict(mu=mu, m_w=cfg["m_w"], k=k0, adapt_every=10, k_max=km, tol=1e-8)
+                      for mu in (cfg["mu"], 0.5 * cfg["mu"], 0.0)]
+            one = ovl.ovl_sign_workspace_bytes(h, params, [None] * 3)
+            assert one > ovl.ovl_sign_workspace_bytes(h, params[:1], [None])
+            batches = predictor.admit(h, params, [None] * 3, one // 2 + 1)
+            assert len(batches) >= 2 and sorted(i for bt in batches for i in bt) == [0, 1, 2]
+            bb = np.stack([b] * 3)
+            y_all = np.zeros_like(bb)
+            inf_all = ovl.ovl_sign_apply(h, params, [None] * 3, bb, y_all)
+            for bt in batches:
+                y = np.zeros((len(bt),) + b.shape, complex)
+                inf = ovl.ovl_sign_apply(h, [params[i] for i in bt], [None] * len(bt), np.stack([b] * len(bt)), y)
+                for j, i in enumerate(bt):
+                    assert np.array_equal(y[j], y_all[i]), (bt, i)
+                    assert inf[j]["k_used"] == inf_all[i]["k_used"]
+            for i, inf in enumerate(inf_all):
+                if inf["k_used"] < params[i]["k_max"]:
+                    assert inf["err_est"] <= 1e-9, (i, inf)
+        finally:
+            ovl.ovl_destroy_lattice(h)

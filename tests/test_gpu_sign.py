@@ -528,3 +528,40 @@ def test_schur_sylvester_route_against_oracle(dims, m, k):
             ovl.ovl_destroy_deflation(d)
     finally:
         ovl.ovl_destroy_lattice(h)
+
+
+@pytest.mark.late
+def test_graph_replay_gives_the_eager_results():
+    """ovl_set_graphs(1): the second call of a batch shape captures the
+    Arnoldi loop into a CUDA graph, later calls replay it; every result equals
+    the eager one bit for bit, a new shape runs eagerly again, and switching
+    graphs off returns to eager launches."""
+    need_gpu()
+    mu, m_w = 0.3, -1.0
+    U, A = _setup(DIMS, 0.5, mu, m_w)
+    S, T, lam, R, L = _schur(A, DIMS, 12)
+    b = synth.gaussian_source(DIMS, 1)
+    h = lattice(DIMS, U)
+    try:
+        ds = _defl_schur(h, mu, m_w, S, T, DIMS)
+        params = [dict(mu=mu, m_w=m_w, k=40), dict(mu=mu, m_w=m_w, k=25), dict(mu=0.1, m_w=m_w, k=33)]
+        bb = np.stack([b, b, b])
+        y0 = np.zeros_like(bb)
+        ovl.ovl_sign_apply(h, params, [ds, None, None], bb, y0)
+        assert ovl.ovl_set_graphs(h, 1) == 0
+        for call in range(4):
+            y = np.zeros_like(bb)
+            ovl.ovl_sign_apply(h, params, [ds, None, None], bb, y)
+            assert np.array_equal(y, y0), call
+        assert ovl.ovl_set_graphs(h, -1) >= 2  # calls 3 and 4 replayed the graph
+        other = [dict(p, k=p["k"] + 1) for p in params]
+        ovl.ovl_sign_apply(h, other, [ds, None, None], bb, y)
+        ref = [krylov.sign_schur(A, b.ravel(), 41, S, T), krylov.sign_arnoldi(A, b.ravel(), 26)]
+        assert rel(y[0], ref[0]) < 1e-10 and rel(y[1], ref[1]) < 1e-10
+        ovl.ovl_set_graphs(h, 0)
+        y = np.zeros_like(bb)
+        ovl.ovl_sign_apply(h, params, [ds, None, None], bb, y)
+        assert np.array_equal(y, y0)
+        ovl.ovl_destroy_deflation(ds)
+    finally:
+        ovl.ovl_destroy_lattice(h)

@@ -86,3 +86,26 @@ def test_random_configs_stay_in_the_training_ranges():
     for _ in range(200):
         c = predictor.random_config(rng)
         assert 0.2 <= c["eps"] <= 0.6 and 0.0 <= c["mu"] <= 0.6 and -1.5 <= c["m_w"] <= -0.8
+
+
+def test_plan_depths_start_at_the_prediction_and_cap_the_basis():
+    from paper_0710_0341_gb300 import predictor
+
+    assert predictor.plan_depths([183.0, 5.0, 900.0]) == [(180, 229), (20, 20), (700, 700)]
+
+
+def test_admit_packs_solves_under_the_budget_first_fit_by_size():
+    from paper_0710_0341_gb300 import predictor
+
+    ks = [300, 100, 250, 50, 200]
+    params = [dict(mu=0.1, m_w=-1.0, k=k) for k in ks]
+    # a stand-in for ovl_sign_workspace_bytes: 1 byte per basis column plus 10 per solve
+    ws = lambda p, d: sum(x["k"] + 1 + 10 for x in p)  # noqa: E731
+    batches = predictor.admit(None, params, [None] * 5, 600, workspace=ws)
+    assert sorted(i for b in batches for i in b) == list(range(5))
+    assert all(ws([params[i] for i in b], None) <= 600 for b in batches)
+    assert batches == [[0, 2], [1, 3, 4]]  # 300 + 250 first, then 200 + 100 + 50
+    import pytest
+
+    with pytest.raises(ValueError):
+        predictor.admit(None, params, [None] * 5, 200, workspace=ws)
