@@ -353,6 +353,11 @@ def main():
     sketch = load_sketch("config3_ystar_sketch.json")
     keys = [f"{s},{c}" for s, c in srcs]
     acc = accuracy(list(yd.cpu().numpy()), sketch, keys)
+    # sgn(sgn(A) b) = b (Eq. 6) for the first source, one more solve outside the timed region
+    zd = torch.zeros_like(bd[:1])
+    ovl.ovl_sign_apply(h, params[:1], defl[:1], yd[:1].contiguous(), zd)
+    involution = float((zd[0] - bd[0]).norm() / bd[0].norm())
+    del zd
     # ---- timed region: device-resident inputs, no per-kernel instrumentation ----
     if ws > 1:
         torch.distributed.barrier()
@@ -427,7 +432,8 @@ def main():
                              "keys": "fmt/links: 0/0 FP64, 1/1 FP32 18-real, 1/2 FP32 12-real"}}
         line.update(extras)
         line["accuracy"] = {"rel_err_per_solve": acc, "meets_1e-8": ok,
-                            "reference": "tests/golden/config3_ystar_sketch.json (oracle y*, probe sketch)"}
+                            "reference": "tests/golden/config3_ystar_sketch.json (oracle y*, probe sketch)",
+                            "involution_residual_source_0": involution}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

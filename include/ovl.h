@@ -326,19 +326,25 @@ int ovl_set_graphs(ovl_lattice lat, int enable, long long* replays);
  * stencil with 12-real and with 18-real links and the FP64 stencil, times
  * every candidate shape on this lattice with nrhs right-hand sides (CUDA
  * events, 5 launches after 2 warm-up launches): 128 consecutive sites per CTA
- * (and for FP64 also 32), and CTAs covering a tx x ty x tz tile of sites
- * at one t (x fastest; tx*ty*tz = 128, or 32 for FP64; only tiles that divide
- * the lattice). The fastest shape per (spinor format, link type) is kept in
- * the handle and used by every later stencil launch on it (the FP64 shape
- * also for OVL_LINKS_F64DF); results do not depend on the shape. Allocates
- * 2 x nrhs complex128 spinors of work space for the call. report (host, may
- * be NULL): up to max_report records of 7 doubles {fmt, links, tpb, tx, ty,
- * tz, microseconds per launch}; *n_report (may be NULL) gets their number. */
+ * (and for FP64 also 32), CTAs covering a tx x ty x tz tile of sites at one t
+ * (x fastest; tx*ty*tz = 128, or 32 for FP64; only tiles that divide the
+ * lattice), and for FP32 a kernel that stages each hop's neighbour spinor and
+ * link in shared memory by asynchronous copies. The fastest shape per (spinor
+ * format, link type) is kept in the handle and used by every later stencil
+ * launch on it (the FP64 shape also for OVL_LINKS_F64DF); results do not
+ * depend on the shape. Allocates 2 x nrhs complex128 spinors of work space for
+ * the call. report (host, may be NULL): up to max_report records of 8 doubles
+ * {fmt, links, tpb, tx, ty, tz, async, microseconds per launch}; *n_report
+ * (may be NULL) gets their number. */
 int ovl_autotune(ovl_lattice lat, int nrhs, double* report, int max_report, int* n_report);
-/* The shape in use for (fmt OVL_VEC_*, links OVL_LINKS_*): {tpb, tx, ty, tz};
- * all zero: the built-in rule (consecutive sites, 128 threads; FP64: 32
+/* The shape in use for (fmt OVL_VEC_*, links OVL_LINKS_*): {tpb, tx, ty, tz,
+ * async}; all zero: the built-in rule (consecutive sites, 128 threads; FP64: 32
  * threads on launches of fewer than 1024 sites per SM). */
-int ovl_autotune_shape(ovl_lattice lat, int fmt, int links, int shape[4]);
+int ovl_autotune_shape(ovl_lattice lat, int fmt, int links, int shape[5]);
+/* Set the shape for (fmt, links) directly (as ovl_autotune_shape reports it);
+ * OVL_EINVAL for a tile that does not divide the lattice, a thread count other
+ * than 128 (or 32 for FP64), or the staged kernel for FP64 spinors. */
+int ovl_autotune_set_shape(ovl_lattice lat, int fmt, int links, const int shape[5]);
 
 /* Failure-detection self test: one CTA waits at a two-member device barrier
  * that nobody else joins, with the same bounded wait the Newton kernel uses

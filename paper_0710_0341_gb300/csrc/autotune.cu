@@ -7,7 +7,9 @@
 // are mostly loaded by the CTA itself and hit L1. Which shape is fastest
 // depends on the lattice, the arithmetic and the number of right-hand sides,
 // so ovl_autotune times every candidate on the lattice's own links and keeps
-// the fastest per (spinor format, link type) in the handle.
+// the fastest per (spinor format, link type) in the handle. For FP32 spinors a
+// further candidate stages each hop's neighbour data in shared memory with
+// asynchronous copies (k_dslash32a).
 #include <string.h>
 
 #include <vector>
@@ -35,6 +37,11 @@ std::vector<Cand> candidates(const ovl_lattice lat, int fp64) {
         c.s.tpb = 32;
         out.push_back(c);
         c.s.tpb = 128;
+        out.push_back(c);
+    } else {
+        c.s = OvlStenShape();  // neighbour data staged by cp.async
+        c.s.tpb = 128;
+        c.s.async = 1;
         out.push_back(c);
     }
     const int sizes[] = {128, 32};
@@ -123,14 +130,15 @@ extern "C" int ovl_autotune(ovl_lattice lat, int nrhs, double* report, int max_r
             cudaEventElapsedTime(&ms, e0, e1);
             const double us = 1e3 * ms / reps;
             if (report && nrep < max_report) {
-                double* q = report + 7 * (size_t)nrep;
+                double* q = report + 8 * (size_t)nrep;
                 q[0] = fmt;
                 q[1] = links;
                 q[2] = c.s.tpb;
                 q[3] = c.s.tx;
                 q[4] = c.s.ty;
                 q[5] = c.s.tz;
-                q[6] = us;
+                q[6] = c.s.async;
+                q[7] = us;
                 nrep++;
             }
             if (us < best) {
@@ -154,7 +162,7 @@ extern "C" int ovl_autotune(ovl_lattice lat, int nrhs, double* report, int max_r
     return rc;
 }
 
-extern "C" int ovl_autotune_shape(ovl_lattice lat, int fmt, int links, int shape[4]) {
+extern "C" int ovl_autotune_shape(ovl_lattice lat, int fmt, int links, int shape[5]) {
     if (!lat || !shape || (fmt != OVL_VEC_F64 && fmt != OVL_VEC_F32) || links < 0 || links > 3)
         return ovl_fail(lat, OVL_EINVAL, "ovl_autotune_shape: bad argument");
     const OvlStenShape& s = lat->sten_shape[fmt == OVL_VEC_F64 ? 0 : 1][links];
@@ -162,5 +170,34 @@ extern "C" int ovl_autotune_shape(ovl_lattice lat, int fmt, int links, int shape
     shape[1] = s.tx;
     shape[2] = s.ty;
     shape[3] = s.tz;
+    shape[4] = s.async;
+    return OVL_OK;
+}
+
+extern "C" int ovl_autotune_set_shape(ovl_lattice lat, int fmt, int links, const int shape[5]) {
+    if (!lat || !shape || (fmt != OVL_VEC_F64 && fmt != OVL_VEC_F32) || links < 0 || links > 3)
+        return ovl_fail(lat, OVL_EINVAL, "ovl_autotune_set_shape: bad argument");
+    OvlStenShape s;
+    s.tpb = shape[0];
+    s.tx = shape[1];
+    s.ty = shape[2];
+    s.tz = shape[3];
+    s.async = shape[4];
+    const int* L = lat->dims;
+    const bool builtin = !s.tpb && !s.tx && !s.ty && !s.tz && !s.async;
+    bool ok = builtin;
+    if (!builtin && s.async)
+        ok = fmt == OVL_VEC_F32 && links != OVL_LINKS_F64 && links != OVL_LINKS_F64DF && s.tpb == 128 && !s.tx &&
+             !s.ty && !s.tz;
+    else if (!builtin && !s.tx)
+        ok = fmt == OVL_VEC_F64 && (s.tpb == 32 || s.tpb == 128) && !s.ty && !s.tz;
+    else if (!builtin)
+        ok = s.tx > 0 && s.ty > 0 && s.tz > 0 && s.tx * s.ty * s.tz == s.tpb &&
+             (s.tpb == 128 || (s.tpb == 32 && fmt == OVL_VEC_F64)) && L[0] % s.tx == 0 && L[1] % s.ty == 0 &&
+             L[2] % s.tz == 0;
+    if (!ok)
+        return ovl_fail(lat, OVL_EINVAL, "ovl_autotune_set_shape: shape {%d,%d,%d,%d,%d} does not fit this lattice/format",
+                        s.tpb, s.tx, s.ty, s.tz, s.async);
+    lat->sten_shape[fmt == OVL_VEC_F64 ? 0 : 1][links] = s;
     return OVL_OK;
 }

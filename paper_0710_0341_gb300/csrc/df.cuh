@@ -77,35 +77,52 @@ DF_HD void dfacc_zero(dfacc& a) {
     a.s = make_float2(0.f, 0.f);
     a.t = make_float2(0.f, 0.f);
 }
-// a += q * g (complex), q = qh + ql, g = gh + gl
+// Paired FP32 operations: the real and imaginary parts of a complex
+// accumulation travel as one float2. On the device these are Blackwell's
+// paired instructions (one instruction, two independent IEEE operations with
+// round-to-nearest, never contracted); on the host the two scalar operations.
+// Either way each component gets exactly the scalar operation's result.
+#ifdef __CUDA_ARCH__
+#define F2_ADD(a, b) __fadd2_rn(a, b)
+#define F2_MUL(a, b) __fmul2_rn(a, b)
+#define F2_FMA(a, b, c) __ffma2_rn(a, b, c)
+#else
+#define F2_ADD(a, b) make_float2(DF_ADD((a).x, (b).x), DF_ADD((a).y, (b).y))
+#define F2_MUL(a, b) make_float2(DF_MUL((a).x, (b).x), DF_MUL((a).y, (b).y))
+#define F2_FMA(a, b, c) make_float2(DF_FMA((a).x, (b).x, (c).x), DF_FMA((a).y, (b).y, (c).y))
+#endif
+DF_HD float2 f2_neg(float2 a) { return make_float2(-a.x, -a.y); }
+// two_sum on both components
+DF_HD void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+    s = F2_ADD(a, b);
+    const float2 bb = F2_ADD(s, f2_neg(a));
+    e = F2_ADD(F2_ADD(a, f2_neg(F2_ADD(s, f2_neg(bb)))), F2_ADD(b, f2_neg(bb)));
+}
+
+// a += q * g (complex), q = qh + ql, g = gh + gl. The real part is
+// qh.x gh.x - qh.y gh.y and the imaginary part qh.x gh.y + qh.y gh.x: as pairs,
+// (qh.x, qh.x) * (gh.x, gh.y) and (qh.y, qh.y) * (-gh.y, gh.x), each product
+// exact as two_prod (p + e), the p's summed into s by two_sum, every rounding
+// error and cross term (hi * lo, lo * hi) into t -- the operations and their
+// order per component are those of the scalar formulation.
 DF_HD void dfacc_mac(dfacc& a, float2 qh, float2 ql, float2 gh, float2 gl) {
-    float p, e, s, err;
-    // real part: qh.x*gh.x - qh.y*gh.y
-    two_prod(qh.x, gh.x, p, e);
-    two_sum(a.s.x, p, s, err);
-    a.s.x = s;
-    a.t.x = DF_ADD(a.t.x, DF_ADD(err, e));
-    two_prod(-qh.y, gh.y, p, e);
-    two_sum(a.s.x, p, s, err);
-    a.s.x = s;
-    a.t.x = DF_ADD(a.t.x, DF_ADD(err, e));
-    a.t.x = fmaf(qh.x, gl.x, a.t.x);
-    a.t.x = fmaf(-qh.y, gl.y, a.t.x);
-    a.t.x = fmaf(ql.x, gh.x, a.t.x);
-    a.t.x = fmaf(-ql.y, gh.y, a.t.x);
-    // imag part: qh.x*gh.y + qh.y*gh.x
-    two_prod(qh.x, gh.y, p, e);
-    two_sum(a.s.y, p, s, err);
-    a.s.y = s;
-    a.t.y = DF_ADD(a.t.y, DF_ADD(err, e));
-    two_prod(qh.y, gh.x, p, e);
-    two_sum(a.s.y, p, s, err);
-    a.s.y = s;
-    a.t.y = DF_ADD(a.t.y, DF_ADD(err, e));
-    a.t.y = fmaf(qh.x, gl.y, a.t.y);
-    a.t.y = fmaf(qh.y, gl.x, a.t.y);
-    a.t.y = fmaf(ql.x, gh.y, a.t.y);
-    a.t.y = fmaf(ql.y, gh.x, a.t.y);
+    const float2 qx = make_float2(qh.x, qh.x), qy = make_float2(qh.y, qh.y);
+    const float2 gr = make_float2(-gh.y, gh.x);  // i * gh
+    float2 p, e, s, err;
+    p = F2_MUL(qx, gh);
+    e = F2_FMA(qx, gh, f2_neg(p));
+    two_sum2(a.s, p, s, err);
+    a.s = s;
+    a.t = F2_ADD(a.t, F2_ADD(err, e));
+    p = F2_MUL(qy, gr);
+    e = F2_FMA(qy, gr, f2_neg(p));
+    two_sum2(a.s, p, s, err);
+    a.s = s;
+    a.t = F2_ADD(a.t, F2_ADD(err, e));
+    a.t = F2_FMA(qx, gl, a.t);
+    a.t = F2_FMA(qy, make_float2(-gl.y, gl.x), a.t);
+    a.t = F2_FMA(make_float2(ql.x, ql.x), gh, a.t);
+    a.t = F2_FMA(make_float2(ql.y, ql.y), gr, a.t);
 }
 // merge b into a (both accumulators)
 DF_HD void dfacc_add(dfacc& a, const dfacc& b) {

@@ -1229,9 +1229,11 @@ int ovl_gs_update(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
     }
     if (b.f64) {
         const size_t dyn64 = (size_t)b.pmax * 2 * sizeof(double2) + OVL_MAXPTR * sizeof(void*);
-        if (dyn64 > 48 * 1024)
+        if (dyn64 > 48 * 1024 && !lat->gs_update64_attr) {  // set once per lattice (not while a graph is captured)
             OVL_CUDA_TRY(lat, cudaFuncSetAttribute(k_gs_update64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)dyn64));
+                                                   64 * 1024));
+            lat->gs_update64_attr = true;
+        }
         k_gs_update64<<<grid, 256, dyn64, st>>>(b, j);
     } else if (b.lo16) {
         static const int minb = getenv("OVL_PASSB_MINB") ? atoi(getenv("OVL_PASSB_MINB")) : 3;

@@ -101,6 +101,7 @@ extern "C" int ovl_destroy_lattice(ovl_lattice lat) {
     if (!lat) return OVL_OK;
     cudaStreamSynchronize(lat->stream);
     if (lat->graph_exec) cudaGraphExecDestroy(lat->graph_exec);
+    if (lat->cap_stream) cudaStreamDestroy(lat->cap_stream);
     free_links(lat->links);
     ovl_prof_flush(lat);
     for (cudaEvent_t e : lat->event_pool) cudaEventDestroy(e);

@@ -43,6 +43,7 @@ struct LinkSet {
 // sites, tpb threads per CTA, tpb = 0: the built-in rule)
 struct OvlStenShape {
     int tpb = 0, tx = 0, ty = 0, tz = 0;
+    int async = 0;  // FP32: neighbour data staged in shared memory by cp.async
 };
 
 struct ovl_lattice_s {
@@ -67,10 +68,13 @@ struct ovl_lattice_s {
     // per-device launch facts of this lattice's device, found on first use
     int gs_dot_occ = 0;            // resident pass-A CTAs per SM
     bool gs_update_attr = false;   // pass B may take more than 48 KB of shared memory
+    bool gs_update64_attr = false; // the same for the FP64 pass B
     // stencil launch shapes per [spinor format F64/F32][link type], set by ovl_autotune
     OvlStenShape sten_shape[2][4];
+    bool sten_async_attr = false;  // the staged FP32 kernels may take 64 KB of shared memory
     // CUDA graph of the fixed-depth Arnoldi loop of ovl_sign_apply (ovl_set_graphs)
     bool graphs = false;
+    cudaStream_t cap_stream = nullptr;  // private stream the loop is captured on
     cudaGraphExec_t graph_exec = nullptr;
     uint64_t graph_key = 0, graph_seen = 0;
     long long graph_kernels = 0, graph_replays = 0;
@@ -121,12 +125,16 @@ struct ovl_deflation_s {
 // Error plumbing
 // ---------------------------------------------------------------------------
 int ovl_fail(ovl_lattice lat, int code, const char* fmt, ...);
+// a failed call's error is also taken off the runtime's last-error slot, so
+// that it is not reported again by the next launch check
 #define OVL_CUDA_TRY(lat, call)                                                      \
     do {                                                                             \
         cudaError_t e__ = (call);                                                    \
-        if (e__ != cudaSuccess)                                                      \
+        if (e__ != cudaSuccess) {                                                    \
+            cudaGetLastError();                                                      \
             return ovl_fail((lat), OVL_ECUDA, "%s failed: %s (%s:%d)", #call,         \
                             cudaGetErrorString(e__), __FILE__, __LINE__);            \
+        }                                                                            \
     } while (0)
 #define OVL_LAUNCH_CHECK(lat)                                                        \
     do {                                                                             \

@@ -930,6 +930,18 @@ static int sign_apply_impl(ovl_lattice lat, int nsolve, const ovl_sign_params* p
         memcpy(&u, &da.kappa, sizeof u);  // baked into the stencil launches
         mix(u);
     }
+    // a failure inside a capture ends the capture (discarding the graph) before returning
+    auto end_capture = [&](int rc) -> int {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (lat->cap_stream && cudaStreamIsCapturing(lat->cap_stream, &cs) == cudaSuccess &&
+            cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(lat->cap_stream, &g);
+            if (g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();
+        return rc;
+    };
     bool replay = graph_ok && lat->graph_exec && lat->graph_key == gkey;
     bool capture = graph_ok && !replay && lat->graph_seen == gkey;
     if (graph_ok && !replay && !capture) lat->graph_seen = gkey;  // first call of this shape runs eagerly
@@ -939,12 +951,19 @@ static int sign_apply_impl(ovl_lattice lat, int nsolve, const ovl_sign_params* p
         lat->graph_replays++;
     }
     const long long launches_before = lat->launches;
+    // the loop's stream: the lattice's, or while capturing a private one (the
+    // lattice's stream may be the legacy default stream, which cannot be
+    // captured); a captured loop only records, the graph then runs on st
+    cudaStream_t lst = st;
     if (capture) {
         if (lat->graph_exec) {
             cudaGraphExecDestroy(lat->graph_exec);
             lat->graph_exec = nullptr;
         }
-        OVL_CUDA_TRY(lat, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        if (!lat->cap_stream) OVL_CUDA_TRY(lat, cudaStreamCreateWithFlags(&lat->cap_stream, cudaStreamNonBlocking));
+        OVL_CUDA_TRY(lat, cudaStreamSynchronize(st));
+        OVL_CUDA_TRY(lat, cudaStreamBeginCapture(lat->cap_stream, cudaStreamCaptureModeThreadLocal));
+        lst = lat->cap_stream;
     }
     for (int j = 1; j <= kmax && !replay; j++) {
         int pmax = 0, nact = 0;
@@ -960,27 +979,27 @@ static int sign_apply_impl(ovl_lattice lat, int nsolve, const ovl_sign_params* p
         da.j = j;
         // algorithmic bytes: stencil 960 B/site (FP64); pass A reads the FP32 high
         // plane and u, w; pass B reads the full basis, u, w and writes u and q
-        ProfScope p0(lat, 0, nact * (double)lat->V * site_bytes, st);
-        if (int rc = ovl_dslash_launch(lat, da, OVL_VEC_F64, links, st)) return rc;
-        p0.end(st);
-        ProfScope p1(lat, 1, colsum * N * 8.0 + nact * 2.0 * N * 16.0, st);
-        if (int rc = ovl_gs_dot(lat, bd, j, st)) return rc;
-        p1.end(st);
-        ProfScope p2(lat, 2, 0.0, st);
-        if (int rc = ovl_gs_reduce(lat, bd, j, st)) return rc;
-        p2.end(st);
-        ProfScope p3(lat, 3, 0.0, st);
-        if (int rc = ovl_gs_small(lat, bd, j, st)) return rc;
-        p3.end(st);
-        ProfScope p4(lat, 4, colsum * N * qbytes + nact * (3.0 * N * 16.0 + N * qbytes), st);
-        if (int rc = ovl_gs_update(lat, bd, j, st)) return rc;
-        p4.end(st);
+        ProfScope p0(lat, 0, nact * (double)lat->V * site_bytes, lst);
+        if (int rc = ovl_dslash_launch(lat, da, OVL_VEC_F64, links, lst)) return end_capture(rc);
+        p0.end(lst);
+        ProfScope p1(lat, 1, colsum * N * 8.0 + nact * 2.0 * N * 16.0, lst);
+        if (int rc = ovl_gs_dot(lat, bd, j, lst)) return end_capture(rc);
+        p1.end(lst);
+        ProfScope p2(lat, 2, 0.0, lst);
+        if (int rc = ovl_gs_reduce(lat, bd, j, lst)) return end_capture(rc);
+        p2.end(lst);
+        ProfScope p3(lat, 3, 0.0, lst);
+        if (int rc = ovl_gs_small(lat, bd, j, lst)) return end_capture(rc);
+        p3.end(lst);
+        ProfScope p4(lat, 4, colsum * N * qbytes + nact * (3.0 * N * 16.0 + N * qbytes), lst);
+        if (int rc = ovl_gs_update(lat, bd, j, lst)) return end_capture(rc);
+        p4.end(lst);
         if (any_adapt)
             if (int rc = adaptive_check(j)) return rc;
     }
     if (capture) {
         cudaGraph_t g = nullptr;
-        OVL_CUDA_TRY(lat, cudaStreamEndCapture(st, &g));
+        OVL_CUDA_TRY(lat, cudaStreamEndCapture(lat->cap_stream, &g));
         const cudaError_t e = cudaGraphInstantiate(&lat->graph_exec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {

@@ -81,6 +81,7 @@ _SIGS = {
     "ovl_set_graphs": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong)]),
     "ovl_autotune": (C.c_int, [_P, C.c_int, _P, C.c_int, C.POINTER(C.c_int)]),
     "ovl_autotune_shape": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "ovl_autotune_set_shape": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "ovl_wait_selftest": (C.c_int, [_P, C.c_longlong, C.POINTER(C.c_int)]),
     "ovl_ritz_values": (C.c_int, [_P, C.c_double, C.c_double, C.c_int, _P, _P]),
     "ovl_profile": (C.c_int, [_P, C.c_int, _P]),
@@ -339,17 +340,22 @@ def ovl_set_graphs(h, enable):
 def ovl_autotune(h, nrhs=1, max_report=256):
     """Time the stencil's launch shapes and keep the fastest per (format,
     links); returns the timed candidates as dicts."""
-    buf = (C.c_double * (7 * max_report))()
+    buf = (C.c_double * (8 * max_report))()
     n = C.c_int()
     _check(lib().ovl_autotune(h, int(nrhs), C.cast(buf, _P), int(max_report), C.byref(n)), h)
-    keys = ("fmt", "links", "tpb", "tx", "ty", "tz", "us")
-    return [dict(zip(keys, [int(buf[7 * i + j]) for j in range(6)] + [buf[7 * i + 6]])) for i in range(n.value)]
+    keys = ("fmt", "links", "tpb", "tx", "ty", "tz", "async", "us")
+    return [dict(zip(keys, [int(buf[8 * i + j]) for j in range(7)] + [buf[8 * i + 7]])) for i in range(n.value)]
 
 
 def ovl_autotune_shape(h, fmt, links):
-    s = (C.c_int * 4)()
+    s = (C.c_int * 5)()
     _check(lib().ovl_autotune_shape(h, int(fmt), int(links), s), h)
     return tuple(s)
+
+
+def ovl_autotune_set_shape(h, fmt, links, shape):
+    s = (C.c_int * 5)(*[int(v) for v in shape])
+    _check(lib().ovl_autotune_set_shape(h, int(fmt), int(links), s), h)
 
 
 def ovl_profile(h, enable):

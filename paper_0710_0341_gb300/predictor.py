@@ -86,6 +86,91 @@ def random_config(rng):
                 m_w=float(rng.uniform(-1.5, -0.8)), seed=int(rng.integers(1 << 30)))
 
 
+# Training data at scale: 6^4 and 8^4 lattices, mu in [0, 1], the m grid below.
+M_GRID_LR = (0, 10, 20, 30, 40, 60)
+
+
+def measure_lr(h, dims, mu, m_w, b, tol=1e-8, k0=20, every=10, k_max=700, sources=12, grid=M_GRID_LR):
+    """For each m of grid: the adaptive depth that reaches tol with LR
+    deflation by the m most critical pairs, all from one setup with the
+    largest m; cost in basis-vector passes k (k/2 + m) plus the setup's
+    passes per source, scaled by m / m_max."""
+    mmax = max(grid)
+    shp = (mmax,) + synth.lattice_shape(dims) + (4, 3)
+    defl = [None]
+    try:
+        d = ovl.ovl_deflation_setup(h, mu, m_w, ovl.OVL_DEFL_LR, mmax, 1e-12, 1000)
+    except ovl.OvlError:
+        d = None
+    setup_each = {0: 0.0}
+    if d is not None:
+        R = np.zeros(shp, np.complex128)
+        L = np.zeros(shp, np.complex128)
+        lam = np.zeros(mmax, np.complex128)
+        ovl.ovl_get_deflation(d, R, lam, L, h)
+        mv = ovl.ovl_deflation_stats(d)[1]
+        ovl.ovl_destroy_deflation(d)
+        for m in grid[1:]:
+            defl.append(ovl.ovl_set_deflation(h, mu, m_w, ovl.OVL_DEFL_LR, m, np.ascontiguousarray(R[:m]),
+                                              np.ascontiguousarray(lam[:m]), np.ascontiguousarray(L[:m])))
+            setup_each[m] = setup_passes(mv, mmax) * (m / mmax) / sources
+    ms = [0] + ([m for m in grid[1:]] if d is not None else [])
+    bb = np.stack([b] * len(ms))
+    y = np.zeros_like(bb)
+    ps = [dict(mu=mu, m_w=m_w, k=k0, adapt_every=every, k_max=k_max, tol=tol)] * len(ms)
+    try:
+        infos = ovl.ovl_sign_apply(h, ps, defl, bb, y)
+    except ovl.OvlError as e:
+        infos = e.infos
+    out = []
+    for m, inf in zip(ms, infos):
+        k = inf["k_used"]
+        ok = inf["status"] == 0 and inf["err_est"] <= tol / 10 and k < k_max
+        out.append(dict(m=m, k=k, ok=bool(ok), cost=k * (k / 2 + m) + setup_each[m], err_est=inf["err_est"]))
+    for m in grid[1:]:
+        if m not in ms:
+            out.append(dict(m=m, k=k_max, ok=False, cost=float("inf"), err_est=None))
+    out.sort(key=lambda r: r["m"])
+    for x in defl[1:]:
+        ovl.ovl_destroy_deflation(x)
+    return out
+
+
+def random_config_scaled(rng):
+    """Training ranges at scale: mu ~ U[0, 1], eps ~ U[0.2, 0.6], m_w ~ U[-1.5, -0.8]."""
+    return dict(eps=float(rng.uniform(0.2, 0.6)), mu=float(rng.uniform(0.0, 1.0)),
+                m_w=float(rng.uniform(-1.5, -0.8)), seed=int(rng.integers(1 << 30)))
+
+
+def generate_scaled(n6, n8, seed=1, path=None, log=print):
+    """Runs of the method on 6^4 (n6) and 8^4 (n8) lattices: features and the
+    cost-minimal (k, m) over M_GRID_LR, written to path after every run."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    t0 = time.time()
+    plan = [(6, 6, 6, 6)] * n6 + [(8, 8, 8, 8)] * n8
+    for i, dims in enumerate(plan):
+        cfg = dict(random_config_scaled(rng), dims=list(dims))
+        U = synth.random_su3_field(dims, cfg["eps"], cfg["seed"])
+        b = synth.gaussian_source(dims, cfg["seed"] + 1)
+        h = ovl.ovl_create_lattice(dims)
+        try:
+            ovl.ovl_set_links(h, U)
+            f = features(h, dims, cfg["mu"], cfg["m_w"], b)
+            res = measure_lr(h, dims, cfg["mu"], cfg["m_w"], b)
+        finally:
+            ovl.ovl_destroy_lattice(h)
+        good = [r for r in res if r["ok"]]
+        best = min(good, key=lambda r: r["cost"]) if good else None
+        rows.append(dict(config=cfg, features=[float(v) for v in f], results=res,
+                         label=None if best is None else [best["k"], best["m"]]))
+        log(f"[{i + 1}/{len(plan)}] {time.time() - t0:.0f}s {dims} label {rows[-1]['label']}")
+        if path:
+            json.dump({"dims": "6^4 and 8^4", "m_grid": list(M_GRID_LR), "scheme": "LR", "rows": rows},
+                      open(path, "w"))
+    return rows
+
+
 def run_config(cfg, dims=(4, 4, 4, 4)):
     U = synth.random_su3_field(dims, cfg["eps"], cfg["seed"])
     b = synth.gaussian_source(dims, cfg["seed"] + 1)

@@ -109,3 +109,59 @@ def test_admit_packs_solves_under_the_budget_first_fit_by_size():
 
     with pytest.raises(ValueError):
         predictor.admit(None, params, [None] * 5, 200, workspace=ws)
+
+
+class _FakeOvlLR:
+    """LR setup with m_max pairs; subsets imported per m; depth falls with m."""
+    OVL_DEFL_LR = 2
+    OvlError = _OvlError
+
+    def __init__(self, k_of_m):
+        self.k_of_m, self.imported, self.destroyed = k_of_m, [], []
+
+    def ovl_deflation_setup(self, h, mu, m_w, scheme, m, tol, max_restarts):
+        assert scheme == 2
+        return ("setup", m)
+
+    def ovl_get_deflation(self, d, R, lam, L, h):
+        R[:] = np.arange(R.shape[0])[(slice(None),) + (None,) * (R.ndim - 1)]
+        lam[:] = np.arange(lam.size) + 0.5
+        L[:] = -R
+        return 2, d[1]
+
+    def ovl_deflation_stats(self, d):
+        return (5, 3000)
+
+    def ovl_set_deflation(self, h, mu, m_w, scheme, m, R, lam, L):
+        assert R.shape[0] == m and lam.size == m and L.shape[0] == m
+        assert np.array_equal(R[:, 0, 0, 0, 0, 0, 0].real, np.arange(m))  # the m most critical, in order
+        self.imported.append(m)
+        return ("lr", m)
+
+    def ovl_sign_apply(self, h, params, defl, b, y):
+        ms = [0 if d is None else d[1] for d in defl]
+        return [dict(status=0, k_used=self.k_of_m[m], err_est=1e-10) for m in ms]
+
+    def ovl_destroy_deflation(self, d):
+        self.destroyed.append(d)
+
+
+def test_measure_lr_uses_one_setup_and_its_leading_pairs(monkeypatch):
+    k_of_m = {0: 400, 10: 300, 20: 250, 30: 220, 40: 210, 60: 200}
+    fake = _FakeOvlLR(k_of_m)
+    monkeypatch.setattr(predictor, "ovl", fake)
+    dims = (2, 2, 2, 2)
+    res = predictor.measure_lr(None, dims, 0.5, -1.0, np.zeros(synth_shape(dims)))
+    assert fake.imported == [10, 20, 30, 40, 60]
+    assert ("setup", 60) in fake.destroyed and len(fake.destroyed) == 6
+    by_m = {r["m"]: r for r in res}
+    sp = predictor.setup_passes(3000, 60) / 12
+    assert by_m[0]["cost"] == 400 * 200
+    assert by_m[30]["cost"] == pytest.approx(220 * (110 + 30) + sp * 30 / 60)
+    assert all(r["ok"] for r in res)
+
+
+def synth_shape(dims):
+    from paper_0710_0341_gb300 import synth
+
+    return synth.lattice_shape(dims) + (4, 3)
