@@ -333,12 +333,15 @@ int ovl_set_graphs(ovl_lattice lat, int enable, long long* replays);
  * format, link type) is kept in the handle and used by every later stencil
  * launch on it (the FP64 shape also for OVL_LINKS_F64DF); results do not
  * depend on the shape. Allocates 2 x nrhs complex128 spinors of work space for
- * the call. report (host, may be NULL): up to max_report records of 8 doubles
- * {fmt, links, tpb, tx, ty, tz, async, microseconds per launch}; *n_report
- * (may be NULL) gets their number. */
+ * the call. For FP32 also the consecutive-site kernel with its registers
+ * capped for 6 and for 4 resident CTAs per SM instead of 8 (fewer spills,
+ * fewer warps). report (host, may be NULL): up to max_report records of 8
+ * doubles {fmt, links, tpb, tx, ty, tz, variant, microseconds per launch},
+ * variant = async (0/1) + 10 x the register cap's CTAs (0: the default 8);
+ * *n_report (may be NULL) gets their number. */
 int ovl_autotune(ovl_lattice lat, int nrhs, double* report, int max_report, int* n_report);
 /* The shape in use for (fmt OVL_VEC_*, links OVL_LINKS_*): {tpb, tx, ty, tz,
- * async}; all zero: the built-in rule (consecutive sites, 128 threads; FP64: 32
+ * variant} as in the report; all zero: the built-in rule (consecutive sites, 128 threads; FP64: 32
  * threads on launches of fewer than 1024 sites per SM). */
 int ovl_autotune_shape(ovl_lattice lat, int fmt, int links, int shape[5]);
 /* Set the shape for (fmt, links) directly (as ovl_autotune_shape reports it);

@@ -43,6 +43,12 @@ std::vector<Cand> candidates(const ovl_lattice lat, int fp64) {
         c.s.tpb = 128;
         c.s.async = 1;
         out.push_back(c);
+        for (int mb : {6, 4}) {  // register caps of 85 and 128 (fewer spills, fewer warps)
+            c.s = OvlStenShape();
+            c.s.tpb = 128;
+            c.s.minb = mb;
+            out.push_back(c);
+        }
     }
     const int sizes[] = {128, 32};
     for (int sz : sizes) {
@@ -137,7 +143,7 @@ extern "C" int ovl_autotune(ovl_lattice lat, int nrhs, double* report, int max_r
                 q[3] = c.s.tx;
                 q[4] = c.s.ty;
                 q[5] = c.s.tz;
-                q[6] = c.s.async;
+                q[6] = c.s.async + 10 * c.s.minb;  // async flag; register cap as 10 x resident CTAs
                 q[7] = us;
                 nrep++;
             }
@@ -170,7 +176,7 @@ extern "C" int ovl_autotune_shape(ovl_lattice lat, int fmt, int links, int shape
     shape[1] = s.tx;
     shape[2] = s.ty;
     shape[3] = s.tz;
-    shape[4] = s.async;
+    shape[4] = s.async + 10 * s.minb;
     return OVL_OK;
 }
 
@@ -182,11 +188,15 @@ extern "C" int ovl_autotune_set_shape(ovl_lattice lat, int fmt, int links, const
     s.tx = shape[1];
     s.ty = shape[2];
     s.tz = shape[3];
-    s.async = shape[4];
+    s.async = shape[4] % 10;
+    s.minb = shape[4] / 10;
     const int* L = lat->dims;
-    const bool builtin = !s.tpb && !s.tx && !s.ty && !s.tz && !s.async;
+    const bool builtin = !s.tpb && !s.tx && !s.ty && !s.tz && !s.async && !s.minb;
     bool ok = builtin;
-    if (!builtin && s.async)
+    if (!builtin && s.minb)
+        ok = fmt == OVL_VEC_F32 && (s.minb == 4 || s.minb == 6) && s.tpb == 128 && !s.tx && !s.async &&
+             links != OVL_LINKS_F64 && links != OVL_LINKS_F64DF;
+    else if (!builtin && s.async)
         ok = fmt == OVL_VEC_F32 && links != OVL_LINKS_F64 && links != OVL_LINKS_F64DF && s.tpb == 128 && !s.tx &&
              !s.ty && !s.tz;
     else if (!builtin && !s.tx)

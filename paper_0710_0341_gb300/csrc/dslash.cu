@@ -55,8 +55,8 @@ __global__ void __launch_bounds__(128) k_dslash(KArgs a) {
 
 // FP32 spinors: at most 64 registers, 8 CTAs per SM (measured 13 % faster
 // than 96 registers with 12-real links at 24^3x48, in spite of a few spills)
-template <typename T, typename VT, int LINKS, bool TILED = false>
-__global__ void __launch_bounds__(128, 8) k_dslash32(KArgs a) {
+template <typename T, typename VT, int LINKS, bool TILED = false, int MINB = 8>
+__global__ void __launch_bounds__(128, MINB) k_dslash32(KArgs a) {
     dslash_site<T, VT, LINKS, TILED>(a);
 }
 
@@ -305,10 +305,18 @@ int ovl_dslash_launch(ovl_lattice lat, const DslashArgs& d, int fmt, int links, 
         }
         else if (links == OVL_LINKS_F32 && t)
             k_dslash32<float, float2, OVL_LINKS_F32, true><<<grid, tpb32, 0, st>>>(a);
+        else if (links == OVL_LINKS_F32 && sh.minb == 6)
+            k_dslash32<float, float2, OVL_LINKS_F32, false, 6><<<grid, tpb32, 0, st>>>(a);
+        else if (links == OVL_LINKS_F32 && sh.minb == 4)
+            k_dslash32<float, float2, OVL_LINKS_F32, false, 4><<<grid, tpb32, 0, st>>>(a);
         else if (links == OVL_LINKS_F32)
             k_dslash32<float, float2, OVL_LINKS_F32><<<grid, tpb32, 0, st>>>(a);
         else if (t)
             k_dslash32<float, float2, OVL_LINKS_R12, true><<<grid, tpb32, 0, st>>>(a);
+        else if (sh.minb == 6)
+            k_dslash32<float, float2, OVL_LINKS_R12, false, 6><<<grid, tpb32, 0, st>>>(a);
+        else if (sh.minb == 4)
+            k_dslash32<float, float2, OVL_LINKS_R12, false, 4><<<grid, tpb32, 0, st>>>(a);
         else
             k_dslash32<float, float2, OVL_LINKS_R12><<<grid, tpb32, 0, st>>>(a);
     }

@@ -16,8 +16,6 @@
 // pass-B arithmetic for whatever coefficients are used, so the inner products
 // of pass A only need FP32 products (they steer orthogonality), while pass B
 // accumulates in double-float (48 bits) against the stored hi+lo basis.
-#include <stdlib.h>
-
 #include <algorithm>
 #include <cmath>
 
@@ -619,6 +617,30 @@ __global__ void __launch_bounds__(256, MINB) k_gs_update(BatchDev B, int j) {
                     }
                 }
             }
+            // the rest (the Schur columns, FP32 low planes, and a last Krylov
+            // column): one column per step, to keep the register peak at the loop above
+            for (int c = c0; c >= 0; c -= 8) {
+                const float4* __restrict__ qh =
+                    (const float4*)(c < nptr ? s_qh[c] : d.vhi + (size_t)(c - nptr) * N);
+                const float4* __restrict__ ql = c < nptr ? (const float4*)s_ql[c] : nullptr;
+                const void* ql16 = c < nptr ? nullptr : (const void*)(vlo16 + (size_t)(c - nptr) * N);
+                const float2 apc = s_ap[c], ghc = s_gh[c], glc = s_gl[c];
+#pragma unroll
+                for (int i = 0; i < UPD_RPL / 2; i++) {
+                    const size_t r = base + 64 * i + 2 * lane;
+                    if (!(full || r < N)) continue;
+                    const float4 hv = __ldg(qh + (r >> 1));
+                    const float4 lv = ql ? __ldg(ql + (r >> 1)) : lo16_pair(ql16, r >> 1);
+                    const float2 h0 = make_float2(hv.x, hv.y), h1 = make_float2(hv.z, hv.w);
+                    sq[2 * i].x = fmaf(h0.x, apc.x, fmaf(-h0.y, apc.y, sq[2 * i].x));
+                    sq[2 * i].y = fmaf(h0.x, apc.y, fmaf(h0.y, apc.x, sq[2 * i].y));
+                    sq[2 * i + 1].x = fmaf(h1.x, apc.x, fmaf(-h1.y, apc.y, sq[2 * i + 1].x));
+                    sq[2 * i + 1].y = fmaf(h1.x, apc.y, fmaf(h1.y, apc.x, sq[2 * i + 1].y));
+                    dfacc_mac(sg[2 * i], h0, make_float2(lv.x, lv.y), ghc, glc);
+                    dfacc_mac(sg[2 * i + 1], h1, make_float2(lv.z, lv.w), ghc, glc);
+                }
+            }
+            c0 = -1;
         }
         for (; c0 >= 0; c0 -= 16) {
             float4 h4[2][UPD_RPL / 2], l4[2][UPD_RPL / 2];
@@ -1221,8 +1243,6 @@ int ovl_gs_update(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
                                                64 * 1024));
         OVL_CUDA_TRY(lat, cudaFuncSetAttribute(k_gs_update<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                64 * 1024));
-        OVL_CUDA_TRY(lat, cudaFuncSetAttribute(k_gs_update<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               64 * 1024));
         OVL_CUDA_TRY(lat, cudaFuncSetAttribute(k_gs_update<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                64 * 1024));
         lat->gs_update_attr = true;
@@ -1236,11 +1256,9 @@ int ovl_gs_update(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
         }
         k_gs_update64<<<grid, 256, dyn64, st>>>(b, j);
     } else if (b.lo16) {
-        static const int minb = getenv("OVL_PASSB_MINB") ? atoi(getenv("OVL_PASSB_MINB")) : 3;
-        if (minb == 2)
-            k_gs_update<2, 2><<<grid, 256, dyn, st>>>(b, j);
-        else
-            k_gs_update<2><<<grid, 256, dyn, st>>>(b, j);
+        // two CTAs per SM without spills (120 registers); at three (80 registers)
+        // it spills and measured 11.3 against 9.4 s of pass B per 16^3x32 step
+        k_gs_update<2, 2><<<grid, 256, dyn, st>>>(b, j);
     }
     else if (b.df)
         k_gs_update<1><<<grid, 256, dyn, st>>>(b, j);

@@ -44,6 +44,7 @@ struct LinkSet {
 struct OvlStenShape {
     int tpb = 0, tx = 0, ty = 0, tz = 0;
     int async = 0;  // FP32: neighbour data staged in shared memory by cp.async
+    int minb = 0;   // FP32, consecutive sites: resident CTAs the registers are capped for (0: 8, or 6 or 4)
 };
 
 struct ovl_lattice_s {

@@ -967,12 +967,13 @@ static int sign_apply_impl(ovl_lattice lat, int nsolve, const ovl_sign_params* p
     }
     for (int j = 1; j <= kmax && !replay; j++) {
         int pmax = 0, nact = 0;
-        double colsum = 0.0;
+        double colsum = 0.0, colsum_s = 0.0;  // basis columns; of them Schur columns
         for (int i = 0; i < nsolve; i++)
             if (j <= P[i].k) {
                 pmax = std::max(pmax, P[i].m_q + j - 1);
                 nact++;
                 colsum += P[i].m_q + j - 1;
+                colsum_s += P[i].m_q;
             }
         if (!nact) break;
         bd.pmax = pmax;
@@ -991,7 +992,9 @@ static int sign_apply_impl(ovl_lattice lat, int nsolve, const ovl_sign_params* p
         ProfScope p3(lat, 3, 0.0, lst);
         if (int rc = ovl_gs_small(lat, bd, j, lst)) return end_capture(rc);
         p3.end(lst);
-        ProfScope p4(lat, 4, colsum * N * qbytes + nact * (3.0 * N * 16.0 + N * qbytes), lst);
+        // the Schur columns keep FP32 low planes (16 B) in the 40-bit form
+        const double bbytes = lo16 ? (colsum - colsum_s) * N * qbytes + colsum_s * N * 16.0 : colsum * N * qbytes;
+        ProfScope p4(lat, 4, bbytes + nact * (3.0 * N * 16.0 + N * qbytes), lst);
         if (int rc = ovl_gs_update(lat, bd, j, lst)) return end_capture(rc);
         p4.end(lst);
         if (any_adapt)

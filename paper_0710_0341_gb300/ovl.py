@@ -343,7 +343,7 @@ def ovl_autotune(h, nrhs=1, max_report=256):
     buf = (C.c_double * (8 * max_report))()
     n = C.c_int()
     _check(lib().ovl_autotune(h, int(nrhs), C.cast(buf, _P), int(max_report), C.byref(n)), h)
-    keys = ("fmt", "links", "tpb", "tx", "ty", "tz", "async", "us")
+    keys = ("fmt", "links", "tpb", "tx", "ty", "tz", "variant", "us")
     return [dict(zip(keys, [int(buf[8 * i + j]) for j in range(7)] + [buf[8 * i + 7]])) for i in range(n.value)]
 
 

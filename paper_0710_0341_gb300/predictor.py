@@ -32,6 +32,7 @@ NRITZ, NFEAT_RITZ = 64, 16
 UNDER_WEIGHT = 4.0
 HERE = os.path.dirname(os.path.abspath(__file__))
 DATA = os.path.join(HERE, "predictor_data.json")
+DATA_SCALED = os.path.join(HERE, "predictor_data_6x4_8x4.json")  # generate_scaled: 6^4 and 8^4, LR, M_GRID_LR
 
 
 def features(h, dims, mu, m_w, b):
@@ -142,14 +143,26 @@ def random_config_scaled(rng):
                 m_w=float(rng.uniform(-1.5, -0.8)), seed=int(rng.integers(1 << 30)))
 
 
-def generate_scaled(n6, n8, seed=1, path=None, log=print):
-    """Runs of the method on 6^4 (n6) and 8^4 (n8) lattices: features and the
-    cost-minimal (k, m) over M_GRID_LR, written to path after every run."""
+def generate_scaled(n6, n8, seed=1, path=None, log=print, seconds=None):
+    """Runs of the method on 6^4 and 8^4 lattices (n6 and n8 of them,
+    interleaved 6^4-first in the proportion n6 : n8): features and the
+    cost-minimal (k, m) over M_GRID_LR, written to path after every run; stops
+    after `seconds` (the runs done so far are kept)."""
     rng = np.random.default_rng(seed)
     rows = []
     t0 = time.time()
-    plan = [(6, 6, 6, 6)] * n6 + [(8, 8, 8, 8)] * n8
+    plan = []
+    i6 = i8 = 0
+    while i6 < n6 or i8 < n8:  # interleave so that a time limit keeps both sizes
+        if i8 >= n8 or (i6 < n6 and i6 * (n8 or 1) <= i8 * (n6 or 1)):
+            plan.append((6, 6, 6, 6))
+            i6 += 1
+        else:
+            plan.append((8, 8, 8, 8))
+            i8 += 1
     for i, dims in enumerate(plan):
+        if seconds is not None and time.time() - t0 > seconds:
+            break
         cfg = dict(random_config_scaled(rng), dims=list(dims))
         U = synth.random_su3_field(dims, cfg["eps"], cfg["seed"])
         b = synth.gaussian_source(dims, cfg["seed"] + 1)
@@ -238,12 +251,29 @@ class Predictor:
         m = np.exp(Y[:, 1]) - 1
         return k, m
 
+    def save(self, path):
+        """Weights (from the device) and the feature standardisation, as .npz."""
+        theta = np.zeros(ovl.ovl_mlp_num_params(self.net), np.float32)
+        ovl.ovl_mlp_get_params(self.net, theta)
+        np.savez(path, theta=theta, mu_x=self.mu_x, sd_x=self.sd_x,
+                 shape=np.array([N_IN, N_HIDDEN, N_OUT], np.int64))
+
+    @classmethod
+    def load(cls, path):
+        z = np.load(path)
+        if tuple(z["shape"]) != (N_IN, N_HIDDEN, N_OUT):
+            raise ValueError(f"{path}: network shape {tuple(z['shape'])}, expected {(N_IN, N_HIDDEN, N_OUT)}")
+        p = cls()
+        ovl.ovl_mlp_set_params(p.net, np.ascontiguousarray(z["theta"], dtype=np.float32))
+        p.mu_x, p.sd_x = z["mu_x"].astype(np.float32), z["sd_x"].astype(np.float32)
+        return p
+
     def close(self):
         ovl.ovl_mlp_destroy(self.net)
 
 
-def nearest_m(m):
-    return min(M_GRID, key=lambda g: abs(g - m))
+def nearest_m(m, grid=M_GRID):
+    return min(grid, key=lambda g: abs(g - m))
 
 
 def plan_depths(k_pred, margin=1.25, k_floor=20, every=10, k_cap=700):

@@ -25,11 +25,15 @@ def _cost(row, m):
     return r["cost"] if r["ok"] else 2.0 * worst  # a choice that never reached 1e-8 is penalised
 
 
-def test_predictor_beats_the_method_without_it():
+@pytest.mark.parametrize("data,grid", [(predictor.DATA, predictor.M_GRID),
+                                       (predictor.DATA_SCALED, predictor.M_GRID_LR)])
+def test_predictor_beats_the_method_without_it(data, grid):
+    """data: runs on 4^4 (Schur, m grid 0..24), or runs on 6^4 and 8^4 with
+    mu up to 1 (LR, m grid 0..60)."""
     need_gpu()
-    if not os.path.exists(predictor.DATA):
+    if not os.path.exists(data):
         pytest.skip("no predictor training data")
-    rows = [r for r in json.load(open(predictor.DATA))["rows"] if r["label"] is not None]
+    rows = [r for r in json.load(open(data))["rows"] if r["label"] is not None]
     assert len(rows) >= 16
     n_tr = (3 * len(rows)) // 4
     train, test = rows[:n_tr], rows[n_tr:]
@@ -42,14 +46,32 @@ def test_predictor_beats_the_method_without_it():
         k_hat, m_hat = p.predict(Xt)
     finally:
         p.close()
-    picks = [predictor.nearest_m(m) for m in m_hat]
+    # the trained network survives a save / load (weights and standardisation)
+    import tempfile
+
+    with tempfile.TemporaryDirectory() as tmp:
+        q = predictor.Predictor(seed=1)
+        try:
+            q.fit(X, T, steps=3000, lr=3e-3)
+            k1, m1 = q.predict(Xt)
+            q.save(os.path.join(tmp, "p.npz"))
+        finally:
+            q.close()
+        r = predictor.Predictor.load(os.path.join(tmp, "p.npz"))
+        try:
+            k2, m2 = r.predict(Xt)
+        finally:
+            r.close()
+        assert np.array_equal(k1, k2) and np.array_equal(m1, m2)
+    picks = [predictor.nearest_m(m, grid) for m in m_hat]
     c_mlp = np.array([_cost(r, m) for r, m in zip(test, picks)])
     c_none = np.array([_cost(r, 0) for r in test])
-    best_fixed = min(predictor.M_GRID, key=lambda m: np.mean([_cost(r, m) for r in train]))
+    best_fixed = min(grid, key=lambda m: np.mean([_cost(r, m) for r in train]))
     c_fixed = np.array([_cost(r, best_fixed) for r in test])
-    c_oracle = np.array([min(_cost(r, m) for m in predictor.M_GRID) for r in test])
-    print(f"held-out mean cost: predictor {c_mlp.mean():.0f}, no deflation {c_none.mean():.0f}, "
-          f"best fixed m={best_fixed} {c_fixed.mean():.0f}, per-config optimum {c_oracle.mean():.0f}")
+    c_oracle = np.array([min(_cost(r, m) for m in grid) for r in test])
+    print(f"{os.path.basename(data)}: {len(train)} training and {len(test)} held-out runs; held-out mean cost: "
+          f"predictor {c_mlp.mean():.0f}, no deflation {c_none.mean():.0f}, best fixed m={best_fixed} "
+          f"{c_fixed.mean():.0f}, per-config optimum {c_oracle.mean():.0f}")
     assert c_mlp.mean() < c_none.mean()
     assert c_mlp.mean() <= 1.05 * c_fixed.mean()
     # the depth estimate sizes the basis: rarely far below the depth needed
