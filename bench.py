@@ -6,11 +6,11 @@ m_w = -1.2, mu = 0.2, the 12 spin-colour point sources at the origin in one
 batched call, Krylov depth k = 600, Schur deflation with m = 40 critical
 eigenvectors. The deflation setup (GPU Krylov-Schur on A^2 with a Chebyshev
 filter; one-off per operator, Sec. 5) runs before the timed region and is
-reported apart. Arithmetic of the timed form ("df40"; --prec df48 for the
-other): FP64 stencil, Krylov basis stored as FP32 hi + BF16 lo (df40, about
-32 significant bits per entry; df48: FP32 hi + lo, 48 bits), FP32 products in
-the pass that only steers orthogonality, double-float accumulation in the
-update pass, projections, recombination and Newton. Beside it, on the same
+reported apart. Arithmetic of the timed form ("df48"; --prec df40 for the
+other): FP64 stencil, Krylov basis stored as FP32 hi + lo (df48, 48
+significant bits per entry; df40: FP32 hi + BF16 lo, about 32 bits), FP32
+products in the pass that only steers orthogonality, double-float
+accumulation in the update pass, projections, recombination and Newton. Beside it, on the same
 inputs: the other basis, the plain FP64 form (complex128 basis, FP64
 arithmetic everywhere) and the mixed forms the workload names (FP32 stencil
 with 12-real links, complex64 basis, FP64 coefficients), each with its
@@ -298,7 +298,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline only (no precision arms, 8^4, stencil)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--prec", default="df40", choices=["df48", "df40"], help="arithmetic of the timed form")
+    ap.add_argument("--prec", default="df48", choices=["df48", "df40"], help="arithmetic of the timed form")
     ap.add_argument("--defl-cache", default=None,
                     help="deflation data file: loaded when it exists (setup skipped), else written after the setup")
     args = ap.parse_args()
@@ -458,7 +458,7 @@ def one_thread_baseline():
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def precision_arms(torch, ovl, h, d, bd, sketch, keys, plain_sources=2, headline="df40"):
+def precision_arms(torch, ovl, h, d, bd, sketch, keys, plain_sources=2, headline="df48"):
     """The other arithmetic forms on the headline inputs and deflation data,
     one step each: the plain FP64 form (on the first plain_sources sources:
     it is bound by the FP64 pipe), the other of the 48-bit and 40-bit bases,

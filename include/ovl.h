@@ -152,9 +152,11 @@ int ovl_apply_Hw(ovl_lattice lat, double mu, double m_w, const double* in, doubl
  * equal ovl_apply_Hw's. Staging uses one fixed 32 MiB device array that every
  * GPU loading the library holds until exit; 2 * nrhs packed spinors plus 24
  * bytes per right-hand side must fit (OVL_EINVAL otherwise). The first call
- * on a device looks up that array's address (cudaGetSymbolAddress) and should
- * come before any stream capture. Calls share the array: calls that overlap
- * on the GPU race. Never calls cudaMalloc or cudaFree. */
+ * on a device looks up that array's address (cudaGetSymbolAddress). Each call
+ * copies a host table and synchronises the lattice's stream, so it may not be
+ * made while that stream is being captured (OVL_EINVAL). Calls share the
+ * array: calls that overlap on the GPU race. Never calls cudaMalloc or
+ * cudaFree. */
 int ovl_apply_Hw_noalloc(ovl_lattice lat, double mu, double m_w, const double* in, double* out,
                          int nrhs, int links);
 
@@ -321,6 +323,20 @@ int ovl_profile(ovl_lattice lat, int enable, double* stats);
  * enable = 0: off (the default; drops the graph); -1: only query.
  * replays (may be NULL): graph replays on this handle so far. */
 int ovl_set_graphs(ovl_lattice lat, int enable, long long* replays);
+
+/* How the Gram-Schmidt update pass (pass B of the Arnoldi step, Eq. 7; the
+ * reorthogonalised column and the next candidate) reads the Krylov basis in
+ * the 48-bit and 40-bit forms (not in the paper; a load strategy only).
+ * bulk = 1: each warp streams its basis columns through a ring of
+ * shared-memory stages filled by asynchronous bulk copies ahead of use;
+ * bulk = 0 (the default): plain register loads, the faster of the two on
+ * GB300 (the per-column bookkeeping of the ring costs more issue slots than
+ * the latency it hides). Both give the same results bit for bit.
+ * The bulk path needs 16-byte aligned columns and N % 4 == 0 (always true for
+ * the library's own workspace); otherwise the register path runs. A stage
+ * wait that times out ends the solve with status OVL_ETIMEOUT. Returns
+ * OVL_EINVAL for bulk outside {0, 1}. */
+int ovl_set_pass_b(ovl_lattice lat, int bulk);
 
 /* Autotuner of the stencil's launch shape (not in the paper). For the FP32
  * stencil with 12-real and with 18-real links and the FP64 stencil, times

@@ -407,6 +407,7 @@ class Solver {
             bd.G = G;
             bd.pstride = pstride;
             bd.df = 1;
+            bd.bulk16 = N % 4 == 0 && (uintptr_t)cur_hi % 16 == 0 && (uintptr_t)cur_lo % 16 == 0;
             if (first) {
                 // v_1 = x/|x| into column 0
                 Mat nn;

@@ -21,6 +21,7 @@
 
 #include <cuda_bf16.h>
 
+#include "bulk.cuh"
 #include "df.cuh"
 #include "krylov.cuh"
 
@@ -739,6 +740,222 @@ __global__ void __launch_bounds__(256, MINB) k_gs_update(BatchDev B, int j) {
 }
 
 // ---------------------------------------------------------------------------
+// pass B with the basis streamed by bulk copies (k_gs_update_bulk). The
+// arithmetic is that of k_gs_update: the same columns per warp (c = p-1-w,
+// p-9-w, ...), the same rows per lane and the same order of operations per
+// accumulator, so the results are bit for bit those of k_gs_update. What
+// differs is how a column reaches the registers: each warp owns a ring of
+// PB_STAGES shared-memory stages; lane 0 fills a stage with one column over
+// the CTA's current row block (cp.async.bulk of the high plane and of the low
+// plane, completed on the stage's mbarrier) PB_STAGES columns ahead of use,
+// continuing into the next row block, so the warp's loads stay in flight while
+// it computes instead of being issued just before the arithmetic.
+// On GB300 it removes the global-load stalls but is the slower path (16^3x32
+// batch: 11.8 against 9.9 s of pass B per step in the 48-bit form, 12.8
+// against 10.0 s in the 40-bit form): the per-column wait, vote and lane-0
+// issue raise the executed instructions by 63 % and the kernel becomes
+// issue-bound, so the register path (k_gs_update) is the default.
+// ---------------------------------------------------------------------------
+constexpr int PB_STAGES = 4;
+constexpr int PB_HI = UPD_RB * (int)sizeof(float2);  // one column's high plane over a row block (1 KB)
+constexpr int PB_STAGE = 2 * PB_HI;                  // + its low plane (FP32; a BF16 plane uses half)
+constexpr int PB_RING = 8 * PB_STAGES * PB_STAGE;    // 8 warps
+constexpr long long PB_MAX_POLLS = 1ll << 22;        // bounded stage waits (seconds)
+
+size_t pb_dyn_bytes(int pmax) {
+    return (size_t)PB_RING + 8 * PB_STAGES * sizeof(uint64_t) + (size_t)pmax * 3 * sizeof(float2) +
+           2 * OVL_MAXPTR * sizeof(void*);
+}
+
+__device__ __forceinline__ float4 lo16_unpack(uint2 v) {  // two rows of BF16 low parts
+    const float2 a = __bfloat1622float2(*(const __nv_bfloat162*)&v.x);
+    const float2 b = __bfloat1622float2(*(const __nv_bfloat162*)&v.y);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+template <int LO>  // 1: FP32 low planes; 2: BF16 low planes of the Krylov columns
+__global__ void __launch_bounds__(256, 2) k_gs_update_bulk(BatchDev B, int j) {
+    const int s = blockIdx.y;
+    SolveDev& d = B.sd[s];
+    if (!solve_in_step(d, j)) return;
+    const int p = solve_p(d, j);
+    const size_t N = B.N;
+    extern __shared__ __align__(128) unsigned char pb_dyn[];
+    unsigned char* ring = pb_dyn;
+    uint64_t* bars = (uint64_t*)(pb_dyn + PB_RING);
+    float2* s_ap = (float2*)(bars + 8 * PB_STAGES);
+    float2* s_gh = s_ap + B.pmax;
+    float2* s_gl = s_gh + B.pmax;
+    const float2** s_qh = (const float2**)(s_gl + B.pmax);
+    const float2** s_ql = s_qh + OVL_MAXPTR;
+    __shared__ float4 red_q[8][UPD_RB / 2];
+    __shared__ float4 red_g[8][UPD_RB];
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nptr = d.nptr;
+    for (int c = tid; c < p; c += 256) {
+        s_ap[c] = d.ap[c];
+        s_gh[c] = d.gh[c];
+        s_gl[c] = d.gl[c];
+    }
+    for (int c = tid; c < nptr && c < p; c += 256) {
+        s_qh[c] = d.qhi[c];
+        s_ql[c] = d.qlo[c];
+    }
+    uint64_t* wbar = bars + warp * PB_STAGES;
+    unsigned char* wring = ring + (size_t)warp * PB_STAGES * PB_STAGE;
+    if (lane == 0)
+        for (int st = 0; st < PB_STAGES; st++) mbar_init(wbar + st, 1);
+    if (tid == 0) abort_flag = 0;
+    mbar_init_fence();
+    const double inv_nu = d.scal[0];
+    const double2 cu = make_double2(d.scal[1], d.scal[2]);
+    float2* qh_out = (float2*)(p < nptr ? d.qhi[p] : d.vhi + (size_t)(p - nptr) * N);
+    float2* ql_out = LO == 1 ? (float2*)(p < nptr ? d.qlo[p] : d.vlo + (size_t)(p - nptr) * N) : nullptr;
+    __nv_bfloat162* ql16_out = LO == 2 ? (__nv_bfloat162*)d.vlo + (size_t)(p - nptr) * N : nullptr;
+    __syncthreads();
+    // this warp's work: row blocks bi of the CTA (grid-stride) x its columns t
+    const int ncw = p - 1 - warp >= 0 ? (p - 1 - warp) / 8 + 1 : 0;
+    const size_t nblk = (N + UPD_RB - 1) / UPD_RB;
+    const int nb = (size_t)blockIdx.x < nblk ? (int)((nblk - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+    const long long nitems = (long long)nb * ncw;
+    auto issue = [&](long long it) {  // lane 0: item it -> stage it % PB_STAGES
+        const int bi = (int)(it / ncw), t = (int)(it - (long long)bi * ncw);
+        const size_t base = ((size_t)blockIdx.x + (size_t)bi * gridDim.x) * UPD_RB;
+        const unsigned rows = (unsigned)((N - base) < (size_t)UPD_RB ? (N - base) : (size_t)UPD_RB);
+        const int c = p - 1 - warp - 8 * t;
+        const void* hs;
+        const void* ls;
+        unsigned lb;
+        if (c < nptr) {
+            hs = s_qh[c] + base;
+            ls = s_ql[c] + base;
+            lb = rows * 8u;
+        } else {
+            const size_t off = (size_t)(c - nptr) * N + base;
+            hs = d.vhi + off;
+            if (LO == 2) {
+                ls = (const __nv_bfloat162*)d.vlo + off;
+                lb = rows * 4u;
+            } else {
+                ls = d.vlo + off;
+                lb = rows * 8u;
+            }
+        }
+        const int st = (int)(it % PB_STAGES);
+        unsigned char* dst = wring + st * PB_STAGE;
+        mbar_arrive_expect_tx(wbar + st, rows * 8u + lb);
+        bulk_copy_g2s(dst, hs, rows * 8u, wbar + st);
+        bulk_copy_g2s(dst + PB_HI, ls, lb, wbar + st);
+    };
+    long long issued = 0;  // lane 0's count
+    if (lane == 0)
+        for (; issued < nitems && issued < PB_STAGES; issued++) issue(issued);
+    long long it = 0;
+    long long landed = 0;  // items whose stage wait completed (all of them unless a wait timed out)
+    bool aborted = false;
+    for (int bi = 0; bi < nb; bi++) {
+        const size_t base = ((size_t)blockIdx.x + (size_t)bi * gridDim.x) * UPD_RB;
+        const bool full = base + UPD_RB <= N;
+        float2 sq[UPD_RPL];
+        dfacc sg[UPD_RPL];
+#pragma unroll
+        for (int i = 0; i < UPD_RPL; i++) {
+            sq[i] = make_float2(0.f, 0.f);
+            dfacc_zero(sg[i]);
+        }
+        for (int t = 0; t < ncw; t++, it++) {
+            if (aborted) continue;
+            const int st = (int)(it % PB_STAGES);
+            const bool ok_wait = *(volatile int*)&abort_flag == 0 &&
+                                 mbar_wait(wbar + st, (unsigned)((it / PB_STAGES) & 1), PB_MAX_POLLS);
+            if (__any_sync(0xffffffffu, !ok_wait)) {  // warp-uniform
+                aborted = true;
+                if (lane == 0) atomicExch(&abort_flag, 1);
+                continue;
+            }
+            landed = it + 1;
+            const int c = p - 1 - warp - 8 * t;
+            const float2 apc = s_ap[c], ghc = s_gh[c], glc = s_gl[c];
+            const unsigned char* sp = wring + st * PB_STAGE;
+            const bool lo32 = LO == 1 || c < nptr;
+#pragma unroll
+            for (int i = 0; i < UPD_RPL / 2; i++) {
+                const bool ok = full || base + 64 * i + 2 * lane < N;
+                const float4 hv = ok ? ((const float4*)sp)[32 * i + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 lv = !ok   ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                  : lo32 ? ((const float4*)(sp + PB_HI))[32 * i + lane]
+                                         : lo16_unpack(((const uint2*)(sp + PB_HI))[32 * i + lane]);
+                const float2 h0 = make_float2(hv.x, hv.y), h1 = make_float2(hv.z, hv.w);
+                // sq += q * ap   (FP32; |ap| is tiny)
+                sq[2 * i].x = fmaf(h0.x, apc.x, fmaf(-h0.y, apc.y, sq[2 * i].x));
+                sq[2 * i].y = fmaf(h0.x, apc.y, fmaf(h0.y, apc.x, sq[2 * i].y));
+                sq[2 * i + 1].x = fmaf(h1.x, apc.x, fmaf(-h1.y, apc.y, sq[2 * i + 1].x));
+                sq[2 * i + 1].y = fmaf(h1.x, apc.y, fmaf(h1.y, apc.x, sq[2 * i + 1].y));
+                dfacc_mac(sg[2 * i], h0, make_float2(lv.x, lv.y), ghc, glc);
+                dfacc_mac(sg[2 * i + 1], h1, make_float2(lv.z, lv.w), ghc, glc);
+            }
+            __syncwarp();
+            if (lane == 0 && issued < nitems) {  // refill this stage PB_STAGES items ahead
+                fence_proxy_async_smem();
+                issue(issued);
+                issued++;
+            }
+        }
+        // cross-warp reduction (as k_gs_update)
+#pragma unroll
+        for (int i = 0; i < UPD_RPL / 2; i++) {
+            int rr = 64 * i + 2 * lane;
+            red_q[warp][rr >> 1] = make_float4(sq[2 * i].x, sq[2 * i].y, sq[2 * i + 1].x, sq[2 * i + 1].y);
+            red_g[warp][rr] = make_float4(sg[2 * i].s.x, sg[2 * i].s.y, sg[2 * i].t.x, sg[2 * i].t.y);
+            red_g[warp][rr + 1] =
+                make_float4(sg[2 * i + 1].s.x, sg[2 * i + 1].s.y, sg[2 * i + 1].t.x, sg[2 * i + 1].t.y);
+        }
+        __syncthreads();
+        if (tid < UPD_RB && *(volatile int*)&abort_flag == 0) {
+            const int rr = tid;
+            const size_t r = base + rr;
+            if (r < N) {
+                float2 tq = make_float2(0.f, 0.f);
+                dfacc tg;
+                dfacc_zero(tg);
+                for (int k = 0; k < 8; k++) {
+                    float4 q4 = red_q[k][rr >> 1];
+                    tq.x += (rr & 1) ? q4.z : q4.x;
+                    tq.y += (rr & 1) ? q4.w : q4.y;
+                    float4 g4 = red_g[k][rr];
+                    dfacc tt;
+                    tt.s = make_float2(g4.x, g4.y);
+                    tt.t = make_float2(g4.z, g4.w);
+                    dfacc_add(tg, tt);
+                }
+                double2 ur = d.u[r], wr = d.w[r];
+                double2 sgv = dfacc_value(tg);
+                double2 q = make_double2(ur.x * inv_nu - (double)tq.x, ur.y * inv_nu - (double)tq.y);
+                double2 un = make_double2(wr.x * inv_nu + (cu.x * ur.x - cu.y * ur.y) - sgv.x,
+                                          wr.y * inv_nu + (cu.x * ur.y + cu.y * ur.x) - sgv.y);
+                float2 qx = split_d(q.x), qy = split_d(q.y);
+                qh_out[r] = make_float2(qx.x, qy.x);
+                if (LO == 1) ql_out[r] = make_float2(qx.y, qy.y);
+                if (LO == 2) ql16_out[r] = __floats2bfloat162_rn(qx.y, qy.y);
+                d.u[r] = un;
+            }
+        }
+        __syncthreads();
+    }
+    if (lane == 0 && issued > landed) {
+        // only after a timed-out or abandoned wait: let this warp's copies in
+        // flight land (bounded) before the CTA's shared memory is released
+        for (long long k = landed; k < issued; k++)
+            mbar_wait(wbar + (int)(k % PB_STAGES), (unsigned)((k / PB_STAGES) & 1), PB_MAX_POLLS);
+    }
+    if (tid == 0 && *(volatile int*)&abort_flag) {
+        atomicExch(&d.status, OVL_ETIMEOUT);
+        d.active = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // accurate projections for deflation, start vectors and the final Galerkin
 // pass: P[c] = Q[:,c]^dag x in double-float (products of the 48-bit basis
 // hi + lo with x split into hi + lo, error about 2^-46 of sum |q| |x|), and
@@ -1255,6 +1472,18 @@ int ovl_gs_update(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
             lat->gs_update64_attr = true;
         }
         k_gs_update64<<<grid, 256, dyn64, st>>>(b, j);
+    } else if (b.df && b.bulk16 && lat->pass_b_bulk && b.pmax <= OVL_MAXCOL) {
+        const size_t dynb = pb_dyn_bytes(b.pmax);
+        if (!lat->gs_bulk_attr) {
+            const int mx = (int)pb_dyn_bytes(OVL_MAXCOL);
+            OVL_CUDA_TRY(lat, cudaFuncSetAttribute(k_gs_update_bulk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+            OVL_CUDA_TRY(lat, cudaFuncSetAttribute(k_gs_update_bulk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+            lat->gs_bulk_attr = true;
+        }
+        if (b.lo16)
+            k_gs_update_bulk<2><<<grid, 256, dynb, st>>>(b, j);
+        else
+            k_gs_update_bulk<1><<<grid, 256, dynb, st>>>(b, j);
     } else if (b.lo16) {
         // two CTAs per SM without spills (120 registers); at three (80 registers)
         // it spills and measured 11.3 against 9.4 s of pass B per 16^3x32 step
@@ -1265,6 +1494,12 @@ int ovl_gs_update(ovl_lattice lat, const BatchDev& b, int j, cudaStream_t st) {
     else
         k_gs_update<0><<<grid, 256, dyn, st>>>(b, j);
     OVL_LAUNCH_CHECK(lat);
+    return OVL_OK;
+}
+
+extern "C" int ovl_set_pass_b(ovl_lattice lat, int bulk) {
+    if (!lat || bulk < 0 || bulk > 1) return ovl_fail(lat, OVL_EINVAL, "ovl_set_pass_b: bad argument");
+    lat->pass_b_bulk = bulk;
     return OVL_OK;
 }
 

@@ -59,6 +59,9 @@ struct BatchDev {
     int f64;         // plain FP64 form: complex128 basis, FP64 products everywhere
     int lo16;        // 40-bit basis: the Krylov columns' low planes are BF16 (vlo holds
                      // __nv_bfloat162 entries); the Schur columns keep FP32 low planes
+    int bulk16;      // set by the caller when every basis column (vhi, vlo and the pointer
+                     // tables) starts on a 16-byte boundary and N % 4 == 0: pass B may then
+                     // stream the columns with bulk copies (ovl_set_pass_b)
 };
 
 // launchers (krylov.cu)

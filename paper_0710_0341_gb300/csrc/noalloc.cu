@@ -13,9 +13,11 @@
 //
 // The host needs the array's device address, which is not the symbol's host
 // name: the first call on each device looks it up with
-// cudaGetSymbolAddress (with that device current) and caches it. That first
-// call should therefore come before any stream capture. All calls share the
-// one array and each overwrites it: calls that overlap on the GPU (several
+// cudaGetSymbolAddress (with that device current) and caches it. Every call
+// copies its pointer table from host memory that is freed on return and then
+// synchronises the lattice's stream, so no call may be made while that stream
+// is being captured into a graph: the call checks and refuses. All calls share
+// the one array and each overwrites it: calls that overlap on the GPU (several
 // streams or threads at once) race and give wrong results.
 #include <string.h>
 
@@ -59,6 +61,11 @@ extern "C" int ovl_apply_Hw_noalloc(ovl_lattice lat, double mu, double m_w, cons
         return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw_noalloc: m_w=%g gives no finite kappa", m_w);
     if (links < OVL_LINKS_F64 || links > OVL_LINKS_F64DF)
         return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw_noalloc: bad links format %d", links);
+    // first, so that a refused call makes no other CUDA call under capture
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    OVL_CUDA_TRY(lat, cudaStreamIsCapturing(lat->stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+        return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw_noalloc: the lattice's stream is being captured");
     if (!ovl_is_device_ptr(in) || !ovl_is_device_ptr(out))
         return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw_noalloc: in and out must be device memory");
     if (in == out) return ovl_fail(lat, OVL_EINVAL, "ovl_apply_Hw_noalloc: in and out must differ");

@@ -70,6 +70,8 @@ struct ovl_lattice_s {
     int gs_dot_occ = 0;            // resident pass-A CTAs per SM
     bool gs_update_attr = false;   // pass B may take more than 48 KB of shared memory
     bool gs_update64_attr = false; // the same for the FP64 pass B
+    bool gs_bulk_attr = false;     // the same for the bulk-copy pass B (its stage ring)
+    int pass_b_bulk = 0;           // 1: pass B streams the basis by bulk copies where it can (ovl_set_pass_b)
     // stencil launch shapes per [spinor format F64/F32][link type], set by ovl_autotune
     OvlStenShape sten_shape[2][4];
     bool sten_async_attr = false;  // the staged FP32 kernels may take 64 KB of shared memory

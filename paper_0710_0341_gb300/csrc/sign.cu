@@ -627,6 +627,7 @@ static int sign_apply_impl(ovl_lattice lat, int nsolve, const ovl_sign_params* p
     bd.df = df;
     bd.f64 = f64;
     bd.lo16 = lo16;
+    bd.bulk16 = N % 4 == 0;  // the basis is carved at 256-byte offsets, the Schur vectors are cudaMalloc'd
     bd.pmax = 0;
     // beta^2 sits in .x of pout3[0]; pass it through a per-solve array
     {

@@ -79,6 +79,7 @@ _SIGS = {
     "ovl_mlp_last_error": (C.c_char_p, [_P]),
     "ovl_link_spread": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "ovl_set_graphs": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong)]),
+    "ovl_set_pass_b": (C.c_int, [_P, C.c_int]),
     "ovl_autotune": (C.c_int, [_P, C.c_int, _P, C.c_int, C.POINTER(C.c_int)]),
     "ovl_autotune_shape": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "ovl_autotune_set_shape": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int)]),
@@ -335,6 +336,11 @@ def ovl_set_graphs(h, enable):
     n = C.c_longlong()
     _check(lib().ovl_set_graphs(h, int(enable), C.byref(n)), h)
     return n.value
+
+
+def ovl_set_pass_b(h, bulk):
+    """1: pass B streams the basis by bulk copies into shared memory; 0: register loads (default)."""
+    _check(lib().ovl_set_pass_b(h, int(bulk)), h)
 
 
 def ovl_autotune(h, nrhs=1, max_report=256):

@@ -1,6 +1,7 @@
 """Host logic of bench.py, on the CPU with stand-ins for the library and for
 torch's device calls (the GPU measurement itself runs only on a GPU)."""
 import numpy as np
+import pytest
 
 import bench
 
@@ -78,15 +79,17 @@ class _Tensor2(_Tensor):
         return self
 
 
-def test_precision_arms_time_each_form_once_on_its_sources(monkeypatch):
+@pytest.mark.parametrize("headline,other,other_prec", [("df48", "df40_bf16_low_planes", 5),
+                                                       ("df40", "df48_fp32_hi_lo_basis", 0)])
+def test_precision_arms_time_each_form_once_on_its_sources(monkeypatch, headline, other, other_prec):
     lib = _Lib()
-    errs = {4: [1e-12, 2e-12], 0: [3e-13] * 12, 2: [6e-8] * 12, 1: [5e-8, None] + [7e-8] * 10}
+    errs = {4: [1e-12, 2e-12], 0: [3e-13] * 12, 5: [6e-11] * 12, 2: [6e-8] * 12, 1: [5e-8, None] + [7e-8] * 10}
     monkeypatch.setattr(bench, "accuracy", lambda ys, sk, keys: errs[lib.calls[-1][0]][:len(keys)])
     bd = _Tensor2(np.ones((12, 4), complex))
-    out = bench.precision_arms(_Torch, lib, None, None, bd, {}, [f"{i}" for i in range(12)])
-    # one call per form: the plain FP64 form on 2 sources, the mixed forms on all 12
-    assert [(c[0], len(c)) for c in lib.calls] == [(4, 2), (0, 12), (2, 12), (1, 12)]
-    assert out["df48_fp32_hi_lo_basis"]["meets_1e-8"] is True
+    out = bench.precision_arms(_Torch, lib, None, None, bd, {}, [f"{i}" for i in range(12)], headline=headline)
+    # one call per form: the plain FP64 form on 2 sources, the other basis and the mixed forms on all 12
+    assert [(c[0], len(c)) for c in lib.calls] == [(4, 2), (other_prec, 12), (2, 12), (1, 12)]
+    assert out[other]["meets_1e-8"] is True
     p = out["plain_fp64"]
     assert p["solves"] == 2 and abs(p["ms_per_step"] - 50.0) < 1e-9 and abs(p["solves_per_s"] - 40.0) < 1e-9
     assert p["meets_1e-8"] is True

@@ -11,7 +11,8 @@ import pytest
 from helpers import lattice, need_gpu, rel, to_dev
 from paper_0710_0341_gb300 import ovl, synth
 
-pytestmark = pytest.mark.gpu
+# late(9): after every other test, the late-marked ones included
+pytestmark = [pytest.mark.gpu, pytest.mark.late(9)]
 
 
 @pytest.mark.parametrize("links,tol", [(ovl.OVL_LINKS_F64, 1e-13), (ovl.OVL_LINKS_R12, 2e-6)])
@@ -72,5 +73,31 @@ def test_noalloc_calls_leave_free_device_memory_unchanged():
             ovl.ovl_apply_Hw_noalloc(h, 0.2, -1.0, x, out, 3, links)
         torch.cuda.synchronize()
         assert torch.cuda.mem_get_info()[0] == free0
+    finally:
+        ovl.ovl_destroy_lattice(h)
+
+
+def test_noalloc_refused_while_the_lattice_stream_is_captured():
+    """Each call copies a host table that is freed on return and synchronises
+    the stream, which a graph cannot hold: under capture the call is refused
+    with OVL_EINVAL before it issues any work, and the capture stays valid."""
+    torch = need_gpu()
+    dims = (2, 2, 2, 4)
+    s = torch.cuda.Stream()
+    h = ovl.ovl_create_lattice(dims, 0, s)
+    try:
+        ovl.ovl_set_links(h, np.ascontiguousarray(synth.unit_gauge_field(dims)))
+        x = to_dev(torch, synth.gaussian_source(dims, 2)[None])
+        out = torch.zeros_like(x)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+            with pytest.raises(ovl.OvlError) as e:
+                ovl.ovl_apply_Hw_noalloc(h, 0.1, -1.0, x, out, 1, ovl.OVL_LINKS_F64)
+            out.add_(1.0)  # the capture still records work after the refusal
+        assert e.value.code == ovl.OVL_EINVAL
+        g.replay()
+        torch.cuda.synchronize()
+        assert float(out.real.min()) == 1.0
     finally:
         ovl.ovl_destroy_lattice(h)
