@@ -176,8 +176,13 @@ int ovl_unpack_spinor(ovl_lattice lat, const void* packed, double* canon, int nr
 /* Import m critical eigenvectors computed elsewhere.
  *  scheme OVL_DEFL_SCHUR: S_or_R = S_m, m orthonormal Schur vectors (m
  *    canonical spinors, one after another); T = T_m, m x m complex128
- *    column-major with A S_m = S_m T_m (upper triangular per Eq. 13; any T
- *    satisfying the relation is accepted); L must be NULL.
+ *    column-major with A S_m = S_m T_m (upper triangular per Eq. 13; the
+ *    Sylvester route, schur_route = 1, needs the triangular form). The
+ *    relation is not checked but is used: the update pass of the Arnoldi
+ *    step takes A S_m from S_m T_m, so data that miss it by delta give
+ *    results off by about delta times the reorthogonalisation coefficients
+ *    (1e-7 of |b| for delta of order one). T may be non-diagonalisable (the
+ *    small sign never forms eigenvectors). L must be NULL.
  *  scheme OVL_DEFL_LR: S_or_R = R_m right eigenvectors, T = Lambda_m (m
  *    complex128 eigenvalues), L = L_m left eigenvectors with L^dag R = I.
  * mu and m_w record the operator the vectors belong to; ovl_sign_apply

@@ -10,7 +10,17 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
                      sign (the matrix iterations Sec. 2 cites):
                      X_0 = A, X_{i+1} = (c_i X_i + X_i^{-1}/c_i)/2 with the
                      determinant scaling c_i = |det X_i|^{-1/n}.  The oracle
-                     uses it only as a second, independent route in tests.
+                     uses it as a second, independent route in tests, and as
+                     the matrix function of the projected matrices when those
+                     are not diagonalisable.
+* ``jordan_form``, ``fun_jordan``, ``sign_jordan`` -- the spectral definition
+                     for a matrix that cannot be diagonalised (Sec. 1, after
+                     Eq. 4: derived from the Cauchy integral, Eq. 3, with the
+                     Jordan decomposition A = X J X^{-1}). On a Jordan block
+                     J_k(l) = l I + N (N the shift, N^k = 0) the integral gives
+                     f(J_k(l)) = sum_{j<k} f^{(j)}(l) / j! N^j; every derivative
+                     of sgn vanishes off the imaginary axis, so
+                     sgn(J_k(l)) = sgn(Re l) I_k.
 """
 from __future__ import annotations
 
@@ -63,3 +73,47 @@ def sign_newton(A: np.ndarray, tol: float = None, max_iter: int = 100):
         if diff <= tol * nrm:
             return X, it
     return X, max_iter
+
+
+def jordan_form(blocks) -> np.ndarray:
+    """J = diag(J_{k_1}(l_1), ...) for blocks [(l_1, k_1), ...]: each block has
+    l on its diagonal and ones on its superdiagonal."""
+    n = sum(int(k) for _, k in blocks)
+    J = np.zeros((n, n), dtype=np.complex128)
+    o = 0
+    for lam, k in blocks:
+        for i in range(int(k)):
+            J[o + i, o + i] = lam
+            if i + 1 < k:
+                J[o + i, o + i + 1] = 1.0
+        o += int(k)
+    return J
+
+
+def fun_jordan(X: np.ndarray, blocks, deriv) -> np.ndarray:
+    """f(A) for A = X J X^{-1}, J = jordan_form(blocks): X diag(f(J_k(l))) X^{-1}
+    with f(J_k(l)) = sum_{j<k} deriv(l, j) / j! N^j, deriv(l, j) = f^{(j)}(l)."""
+    n = X.shape[0]
+    F = np.zeros((n, n), dtype=np.complex128)
+    o = 0
+    for lam, k in blocks:
+        k = int(k)
+        N = np.eye(k, k, 1, dtype=np.complex128)
+        Nj = np.eye(k, dtype=np.complex128)
+        fact = 1.0
+        for j in range(k):
+            if j > 0:
+                Nj = Nj @ N
+                fact *= j
+            F[o:o + k, o:o + k] += deriv(lam, j) / fact * Nj
+        o += k
+    return X @ F @ np.linalg.inv(X)
+
+
+def sign_jordan(X: np.ndarray, blocks) -> np.ndarray:
+    """sgn(A) for A = X J X^{-1} (no eigenvalue on the imaginary axis): the
+    Jordan-form definition with f = sgn, whose derivatives all vanish."""
+    for lam, _ in blocks:
+        if np.real(lam) == 0.0:
+            raise ValueError("sgn is undefined for an eigenvalue on the imaginary axis")
+    return fun_jordan(X, blocks, lambda lam, j: np.sign(np.real(lam)) if j == 0 else 0.0)

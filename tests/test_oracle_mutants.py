@@ -19,6 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 OP, SIGN, KRY, OVL, MLP = ("test_oracle_operator.py", "test_oracle_sign.py", "test_oracle_krylov.py",
                            "test_oracle_overlap.py", "test_oracle_mlp.py")
+JOR = "test_oracle_jordan.py"
 
 # (name, module, text in the oracle, planted replacement, pin files)
 CASES = [
@@ -49,6 +50,16 @@ CASES = [
      "return (U * s[None, :]) @ np.linalg.inv(U)", "return (U * s[:, None]) @ np.linalg.inv(U)", [SIGN]),
     ("Newton: scaling applied twice", "oracle.matfunc",
      "Xn = 0.5 * (c * X + Xi / c)", "Xn = 0.5 * (c * X + Xi * c)", [SIGN]),
+    # the Jordan-form definition (Sec. 1, after Eq. 4)
+    ("Jordan: 1/j instead of 1/j!", "oracle.matfunc", "                fact *= j\n", "                fact = j\n",
+     [JOR]),
+    ("Jordan: ones below instead of above the diagonal", "oracle.matfunc",
+     "J[o + i, o + i + 1] = 1.0", "J[o + i + 1, o + i] = 1.0", [JOR]),
+    ("Jordan: X^-1 f(J) X", "oracle.matfunc", "return X @ F @ np.linalg.inv(X)",
+     "return np.linalg.inv(X) @ F @ X", [JOR]),
+    ("Jordan: sgn keeps a first-derivative term", "oracle.matfunc",
+     "np.sign(np.real(lam)) if j == 0 else 0.0", "np.sign(np.real(lam)) if j == 0 else (0.5 if j == 1 else 0.0)",
+     [JOR]),
     ("free field: mu enters p4 with the wrong sign", "oracle.freefield",
      "pt = [X, Y, Z, T - 1j * mu]", "pt = [X, Y, Z, T + 1j * mu]", [OP, SIGN]),
     ("free field: factor 4 kappa^2 halved", "oracle.freefield",
@@ -115,7 +126,7 @@ def test_unplanted_copies_pass_every_pin():
     mods = ["oracle.dirac", "oracle.matfunc", "oracle.freefield", "oracle.krylov", "oracle.eigen",
             "oracle.overlap", "oracle.mlp"]
     same = "TEST INFRASTRUCTURE ONLY"
-    cases = [("unchanged " + m, m, same, same, [OP, SIGN, KRY, OVL, MLP]) for m in mods]
+    cases = [("unchanged " + m, m, same, same, [OP, SIGN, KRY, OVL, MLP, JOR]) for m in mods]
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         results = list(ex.map(_run, cases))
     bad = [(c[0], rc, out) for c, (rc, out) in zip(cases, results) if rc != 0]
