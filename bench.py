@@ -572,7 +572,12 @@ def extra_12x4(torch, ovl, synth, kmin=150, kmax=700, every=25):
         params = [dict(mu=mu, m_w=-1.0, k=k) for mu, k in zip(mu_of, ks)]
         out = {"solves": len(params), "k_per_mu": {f"{mu}": sorted({k for k, x in zip(ks, mu_of) if x == mu})
                                                      for mu in mus},
-               "adaptive_err_est_max": max(i["err_est"] for i in infos), "setup_s": setup_s}
+               "adaptive_err_est_max": max(i["err_est"] for i in infos),
+               "adaptive_err_est_max_per_mu": {f"{mu}": max(i["err_est"] for i, x in zip(infos, mu_of) if x == mu)
+                                               for mu in mus},
+               "err_est_below_1e-8_per_mu": {f"{mu}": all(i["err_est"] <= 1e-8 for i, x in zip(infos, mu_of) if x == mu)
+                                     for mu in mus},
+               "setup_s": setup_s}
         for name, g in (("eager", 0), ("graph", 1)):
             ovl.ovl_set_graphs(h, g)
             for _ in range(2):  # the second call of a shape captures the graph

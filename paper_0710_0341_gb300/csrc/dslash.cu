@@ -18,15 +18,26 @@ __device__ __forceinline__ void dslash_site(const KArgs& a) {
     const int r = blockIdx.y;
     if (a.active && !a.active[(size_t)r * a.stride]) return;  // whole CTA (one right-hand side)
     if (a.klim && a.j > a.klim[(size_t)r * a.stride]) return;
-    // e^{+-mu} of this right-hand side, once per CTA: an FP64 exp per thread
-    // kept the FP64 pipe half busy in the FP32 kernel
-    __shared__ T s_w[2];
-    if (threadIdx.x == 0) {
-        const double mu = a.mu[r];
-        s_w[0] = (T)exp(mu);
-        s_w[1] = (T)exp(-mu);
+    // e^{+-mu} of this right-hand side. FP32 spinors: every thread takes the
+    // FP32 exponentials itself (no barrier; the FP32 weights carry the FP32
+    // kernel's own rounding). FP64 spinors: one thread per CTA in FP64 (an FP64
+    // exp per thread would add to the FP64 pipe that bounds that kernel).
+    T w_fw, w_bw;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        const float mu = (float)a.mu[r];
+        w_fw = expf(mu);
+        w_bw = expf(-mu);
+    } else {
+        __shared__ T s_w[2];
+        if (threadIdx.x == 0) {
+            const double mu = a.mu[r];
+            s_w[0] = (T)exp(mu);
+            s_w[1] = (T)exp(-mu);
+        }
+        __syncthreads();
+        w_fw = s_w[0];
+        w_bw = s_w[1];
     }
-    __syncthreads();
     size_t site;
     if constexpr (TILED) {  // block -> (tile x, y, z, t), thread -> site in the tile
         unsigned b = blockIdx.x;
@@ -43,7 +54,7 @@ __device__ __forceinline__ void dslash_site(const KArgs& a) {
         site = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     }
     if (site >= a.V) return;
-    site_compute<T, VT, LINKS>(a, (const VT*)a.in[r], (VT*)a.out[r], site, s_w[0], s_w[1]);
+    site_compute<T, VT, LINKS>(a, (const VT*)a.in[r], (VT*)a.out[r], site, w_fw, w_bw);
 }
 
 // FP64 spinors: the compiler's register choice (140 for FP64 links, 168 for the
@@ -155,13 +166,8 @@ __global__ void __launch_bounds__(AS_T, 5) k_dslash32a(KArgs a) {
     const int r = blockIdx.y;
     if (a.active && !a.active[(size_t)r * a.stride]) return;
     if (a.klim && a.j > a.klim[(size_t)r * a.stride]) return;
-    __shared__ float s_w[2];
-    if (threadIdx.x == 0) {
-        const double mu = a.mu[r];
-        s_w[0] = (float)exp(mu);
-        s_w[1] = (float)exp(-mu);
-    }
-    __syncthreads();
+    const float mu_r = (float)a.mu[r];  // as in dslash_site: FP32 weights per thread
+    const float w_fw = expf(mu_r), w_bw = expf(-mu_r);
     const size_t site = blockIdx.x * (size_t)AS_T + threadIdx.x;
     if (site >= a.V) return;
     const float4* in = (const float4*)a.in[r];
@@ -182,7 +188,7 @@ __global__ void __launch_bounds__(AS_T, 5) k_dslash32a(KArgs a) {
     const size_t zm = z == 0 ? site + (Lz - 1) * sz : site - sz;
     const size_t tp = t + 1 == Lt ? site - (Lt - 1) * stt : site + stt;
     const size_t tm = t == 0 ? site + (Lt - 1) * stt : site - stt;
-    float wtp = s_w[0], wtm = s_w[1];
+    float wtp = w_fw, wtm = w_bw;
     if (a.apbc) {
         if (t + 1 == Lt) wtp = -wtp;
         if (t == 0) wtm = -wtm;

@@ -12,8 +12,9 @@ so the expensive eigensolver setup is skipped), inside an NVTX range
     ncu --set full --clock-control none -k regex:k_gs_update -s 200 -c 1 \\
         python tests/profile_case.py
 
-``python tests/profile_case.py stencil r12`` instead applies the stencil alone
-(24^3x48, one right-hand side, 12-real links) five times;
+``python tests/profile_case.py stencil r12 [tuned]`` instead applies the
+stencil alone (24^3x48, one right-hand side, 12-real links) five times, with
+the built-in launch shape or the autotuner's;
 ``python tests/profile_case.py c3 [prec]`` runs one solve of the 16^3x32
 workload's shape at reduced depth (one point source, k = 120, m = 40 Schur
 vectors from a seeded orthonormal block; prec 0 = the 48-bit mode,
@@ -56,20 +57,28 @@ def main():
     print("profile case done; newton iterations", [i["newton_iters"] for i in infos])
 
 
-def stencil(fmt_name="r12", dims=(24, 24, 24, 48), reps=5):
-    """Repeated single-RHS stencil applications on packed spinors (24^3x48)."""
+def stencil(fmt_name="r12", tuned="", dims=(24, 24, 24, 48), reps=5):
+    """Repeated single-RHS stencil applications on packed spinors (24^3x48),
+    inside an NVTX range "stencil"; with "tuned" the launch shapes are first
+    chosen by the autotuner (the shape the benchmark's stencil line uses)."""
     build.build()
     V = int(np.prod(dims))
     h = ovl.ovl_create_lattice(dims)
     ovl.ovl_set_links(h, torch.from_numpy(synth.random_su3_field(dims, 0.3, 0)).cuda())
     fmt, links = {"r12": (1, 2), "f32": (1, 1), "f64": (0, 0)}[fmt_name]
+    if tuned == "tuned":
+        ovl.ovl_autotune(h, 1)
+        print("autotuned shape", ovl.ovl_autotune_shape(h, fmt, links))
     x = torch.randn(12 * V, dtype=torch.complex64 if fmt == 1 else torch.complex128, device="cuda")
     o = torch.zeros_like(x)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("stencil")
     for _ in range(reps):
         ovl.ovl_apply_Hw_packed(h, [0.3], -1.0, x, o, 1, fmt, links)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     ovl.ovl_destroy_lattice(h)
-    print("stencil case done", fmt_name, dims)
+    print("stencil case done", fmt_name, tuned or "built-in shape", dims)
 
 
 def config3(prec=0, k=120, m=40):
@@ -96,7 +105,7 @@ def config3(prec=0, k=120, m=40):
 
 if __name__ == "__main__":
     if len(sys.argv) > 1 and sys.argv[1] == "stencil":
-        stencil(*(sys.argv[2:3] or ["r12"]))
+        stencil(*(sys.argv[2:4] or ["r12"]))
     elif len(sys.argv) > 1 and sys.argv[1] == "c3":
         config3(*(sys.argv[2:3] or [0]))
     else:
