@@ -15,7 +15,7 @@ so the expensive eigensolver setup is skipped), inside an NVTX range
 ``python tests/profile_case.py stencil r12 [tuned]`` instead applies the
 stencil alone (24^3x48, one right-hand side, 12-real links) five times, with
 the built-in launch shape or the autotuner's;
-``python tests/profile_case.py c3 [prec]`` runs one solve of the 16^3x32
+``python tests/profile_case.py c3 [prec [bulk]]`` runs one solve of the 16^3x32
 workload's shape at reduced depth (one point source, k = 120, m = 40 Schur
 vectors from a seeded orthonormal block; prec 0 = the 48-bit mode,
 4 = plain FP64, 2 = mixed with 12-real links).
@@ -81,13 +81,16 @@ def stencil(fmt_name="r12", tuned="", dims=(24, 24, 24, 48), reps=5):
     print("stencil case done", fmt_name, tuned or "built-in shape", dims)
 
 
-def config3(prec=0, k=120, m=40):
+def config3(prec=0, load="", k=120, m=40):
     """One solve of the 16^3x32 workload's shape (point source at the origin,
-    mu = 0.2, m_w = -1.2) at depth k with m seeded orthonormal Schur vectors."""
+    mu = 0.2, m_w = -1.2) at depth k with m seeded orthonormal Schur vectors;
+    load "bulk" streams pass B's columns by bulk copies (ovl_set_pass_b)."""
     build.build()
     dims = (16, 16, 16, 32)
     N = 12 * int(np.prod(dims))
     h = ovl.ovl_create_lattice(dims)
+    if load == "bulk":
+        ovl.ovl_set_pass_b(h, 1)
     ovl.ovl_set_links(h, torch.from_numpy(synth.random_su3_field(dims, 0.3, 0)).cuda())
     rng = np.random.default_rng(0)
     Q, _ = np.linalg.qr(rng.standard_normal((N, m)) + 1j * rng.standard_normal((N, m)))
@@ -107,6 +110,6 @@ if __name__ == "__main__":
     if len(sys.argv) > 1 and sys.argv[1] == "stencil":
         stencil(*(sys.argv[2:4] or ["r12"]))
     elif len(sys.argv) > 1 and sys.argv[1] == "c3":
-        config3(*(sys.argv[2:3] or [0]))
+        config3(*(sys.argv[2:4] or [0]))
     else:
         main()
