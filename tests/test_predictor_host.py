@@ -165,3 +165,56 @@ def synth_shape(dims):
     from paper_0710_0341_gb300 import synth
 
     return synth.lattice_shape(dims) + (4, 3)
+
+
+class _FakeOvlLattice:
+    def __init__(self):
+        self.created = []
+        self.destroyed = 0
+
+    def ovl_create_lattice(self, dims, *a):
+        self.created.append(tuple(dims))
+        return len(self.created)
+
+    def ovl_set_links(self, h, U):
+        pass
+
+    def ovl_destroy_lattice(self, h):
+        self.destroyed += 1
+
+
+def test_generate_scaled_interleaves_sizes_labels_and_stops_on_time(monkeypatch, tmp_path):
+    import json
+
+    fake = _FakeOvlLattice()
+    monkeypatch.setattr(predictor, "ovl", fake)
+    monkeypatch.setattr(predictor.synth, "random_su3_field", lambda dims, eps, seed: np.zeros(1))
+    monkeypatch.setattr(predictor.synth, "gaussian_source", lambda dims, seed: np.zeros(1))
+    monkeypatch.setattr(predictor, "features", lambda h, dims, mu, m_w, b: np.full(20, float(dims[0])))
+    calls = []
+
+    def measure_lr(h, dims, mu, m_w, b):
+        calls.append(dims)
+        if len(calls) == 3:  # a run where no m reached the target: no label
+            return [dict(m=m, k=700, ok=False, cost=float("inf"), err_est=1e-3) for m in predictor.M_GRID_LR]
+        return [dict(m=m, k=300 - m, ok=True, cost=1000.0 + (m - 20) ** 2, err_est=1e-10)
+                for m in predictor.M_GRID_LR]
+
+    monkeypatch.setattr(predictor, "measure_lr", measure_lr)
+    path = str(tmp_path / "runs.json")
+    rows = predictor.generate_scaled(4, 2, seed=3, path=path, log=lambda s: None)
+    # 6^4 first, in the proportion 4 : 2 throughout
+    assert [d[0] for d in fake.created] == [6, 8, 6, 6, 8, 6]
+    assert fake.destroyed == 6 and len(rows) == 6
+    assert rows[2]["label"] is None
+    assert all(r["label"] == [280, 20] for i, r in enumerate(rows) if i != 2)  # the cost-minimal ok entry
+    assert all(0.0 <= r["config"]["mu"] <= 1.0 and list(r["config"]["dims"])[0] == r["features"][0] for r in rows)
+    saved = json.load(open(path))
+    assert len(saved["rows"]) == 6 and saved["m_grid"] == list(predictor.M_GRID_LR)
+    # a time limit keeps the runs done so far (checked before each run): the
+    # clock reads start, then per run the check and the log line
+    t = iter([0.0, 0.0, 5.0, 10.0, 15.0] + [1e6] * 20)
+    monkeypatch.setattr(predictor.time, "time", lambda: next(t))
+    fake.created.clear()
+    rows = predictor.generate_scaled(4, 2, seed=3, path=None, log=lambda s: None, seconds=100)
+    assert len(rows) == 2 and [d[0] for d in fake.created] == [6, 8]
