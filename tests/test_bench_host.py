@@ -233,3 +233,82 @@ def test_amortised_throughput_includes_the_setup():
     a = bench.amortised(100.0, 250.0, 8)
     assert abs(a["1_batches_per_setup"] - 8 / 100.25) < 1e-12
     assert abs(a["12_batches_per_setup"] - 96 / 103.0) < 1e-12
+
+
+class _UnevenLib:
+    """ovl stand-in for the uneven 12^4 batch: adaptive depths by mu, the mu = 0.8
+    solves capped at k_max with a large estimate."""
+    OVL_DEFL_SCHUR = 1
+
+    def __init__(self):
+        self.graphs = 0
+        self.replays = 0
+        self.calls = []
+        self.live = set()
+
+    def ovl_create_lattice(self, dims, apbc, stream):
+        self.live.add("lat")
+        return "lat"
+
+    def ovl_set_links(self, h, U):
+        pass
+
+    def ovl_autotune(self, h, nrhs):
+        return []
+
+    def ovl_deflation_setup(self, h, mu, m_w, scheme, m, tol, maxit):
+        self.live.add(("d", mu))
+        return ("d", mu)
+
+    def ovl_sign_apply(self, h, params, defl, b, y):
+        self.calls.append([dict(p) for p in params])
+        if self.graphs:
+            self.replays += 1
+        out = []
+        for p in params:
+            if "adapt_every" in p:
+                k, e = {0.05: (250, 5e-10), 0.2: (275, 6e-10), 0.4: (350, 8e-10), 0.8: (700, 4e-5)}[p["mu"]]
+            else:
+                k, e = p["k"], 0.0
+            out.append(dict(status=0, k_used=k, err_est=e))
+        return out
+
+    def ovl_set_graphs(self, h, g):
+        if g >= 0:
+            self.graphs = g
+        return self.replays
+
+    def ovl_destroy_deflation(self, d):
+        self.live.discard(d)
+
+    def ovl_destroy_lattice(self, h):
+        self.live.discard(h)
+
+
+class _Torch3(_Torch):
+    @staticmethod
+    def from_numpy(a):
+        t = _Tensor(a)
+        t.cuda = lambda: t
+        return t
+
+
+class _Synth3(_Synth):
+    @staticmethod
+    def point_source(dims, s, c):
+        return np.zeros(2, complex)
+
+
+def test_uneven_batch_reports_depths_and_estimates_per_mu():
+    lib = _UnevenLib()
+    out = bench.extra_12x4(_Torch3, lib, _Synth3)
+    assert not lib.live  # lattice and the four deflation objects released
+    assert out["solves"] == 48
+    assert out["k_per_mu"] == {"0.05": [250], "0.2": [275], "0.4": [350], "0.8": [700]}
+    assert out["adaptive_err_est_max_per_mu"]["0.8"] == 4e-5 and out["adaptive_err_est_max_per_mu"]["0.2"] == 6e-10
+    assert out["err_est_below_1e-8_per_mu"] == {"0.05": True, "0.2": True, "0.4": True, "0.8": False}
+    # the timed calls run the adaptive depths as fixed depths, eager and as graph replays
+    timed = lib.calls[1:]
+    assert len(timed) == 8 and all(len(c) == 48 and "adapt_every" not in c[0] for c in timed)
+    assert sorted({p["k"] for p in timed[0]}) == [250, 275, 350, 700]
+    assert out["graph_replays"] == 4 and "eager" in out and "graph" in out
